@@ -305,44 +305,98 @@ def test_decode_invariants_and_recovery_on_small_config(quantised):
         assert np.abs(x - I.x).sum() / xl1 <= tol
 
 
-def test_one_round_is_jacobi_and_matches_a_literal_python_round():
-    # A pure-Python restatement of one round on a small case: per column, the score of
-    # every anchor from the same residual (synchronous update), then H_k and r = y - A x'.
-    # It shares only log_posterior (pinned above) with the C loop.
-    cfg = dict(n=300, m=90, k=8, d=5, sigma_n=1e-2)
-    I, y = _instance(cfg, 2)
-    rho = I.k / I.m
+def _perturbed_states(I, y, rng):
+    """Injected states (x_hat, r_hat = y - A x_hat) near the truth: some support entries
+    shifted, some dropped, some spurious entries added."""
     A = _A(I.rows, I.m)
+    out = []
+    for frac_shift, frac_drop, n_spur in ((0.3, 0.0, 0), (0.2, 0.3, 3), (0.0, 0.5, 0)):
+        xh = I.x.astype(np.float64).copy()
+        supp = I.support
+        sh = rng.choice(supp, max(1, int(frac_shift * supp.size)), replace=False) if frac_shift else []
+        xh[sh] += rng.choice([-1, 1], len(sh)) * rng.uniform(0.2, 1.0, len(sh))
+        dr = rng.choice(supp, int(frac_drop * supp.size), replace=False) if frac_drop else []
+        xh[dr] = 0.0
+        off = np.setdiff1d(np.arange(I.n), supp)
+        xh[rng.choice(off, n_spur, replace=False)] = rng.uniform(0.3, 1.0, n_spur)
+        out.append((xh, y - A @ xh))
+    return out
+
+
+def _python_round(I, y, xh, rh, t, quantised, alpha):
+    """Alg. 2's loop body restated in plain Python for one column at a time."""
+    rho = I.k / I.m
+    xp = xh.copy()
+    for j in range(I.n):
+        rl = rh[I.rows[j]]
+        lz = oracle.log_posterior("z", rl, I.d, rho, 1.0, I.sigma_n)
+        qz = (lz >= math.log(1 - t)).astype(float) if quantised else np.exp(lz)
+        best = None
+        for s in range(I.d):
+            if not lz[s] <= math.log(1 - t):
+                continue
+            le = oracle.log_posterior("e", rl[s] - rl, I.d, rho, 1.0, I.sigma_n)
+            qe = (le >= math.log(t)).astype(float) if quantised else np.exp(le)
+            ne, nzv = qe.sum(), qz.sum()
+            w = (rl * qe).sum() / ne
+            if np.abs(rl - w).sum() <= np.abs(rl).sum() and ne - nzv >= alpha:
+                if best is None or ne - nzv > best[0]:
+                    best = (ne - nzv, w)
+        if best is not None:
+            xp[j] = xh[j] + best[1]
+    nz = np.nonzero(xp)[0]
+    keep = nz[np.lexsort((nz, -np.abs(xp[nz])))][:I.k]
+    xk = np.zeros_like(xp)
+    xk[keep] = xp[keep]
+    return xk
+
+
+def test_one_round_matches_a_literal_python_round():
+    # A pure-Python restatement of one round: per column, the score of every anchor from
+    # the same residual (synchronous update), then H_k and r = y - A x'.  It shares only
+    # log_posterior (pinned above against Monte-Carlo) with the C loop.
+    cfg = dict(n=600, m=180, k=16, d=5, sigma_n=1e-2)
+    I, y = _instance(cfg, 2)
+    A = _A(I.rows, I.m)
+    rng = np.random.default_rng(5)
+    total_upd = 0
     for quantised in (False, True):
-        c = oracle.default_c(quantised, I.m / I.n, rho)
+        c = oracle.default_c(quantised, I.m / I.n, I.k / I.m)
         alpha = I.d // 2 + 1 if quantised else I.d / 2
-        xh, st, _ = oracle.decode(I.rows, y, I.k, sigma_n=I.sigma_n, quantised=quantised, max_rounds=2)
-        rh = y - A @ xh
-        for ridx in (1, 3, 6):
-            t = 1 - ridx * c
-            xp_c, rp_c, upd, rec = oracle.round_step(I.rows, y, I.k, ridx, xh, rh, sigma_n=I.sigma_n,
-                                                     quantised=quantised)
-            xp = xh.copy()
-            for j in range(I.n):
-                rl = rh[I.rows[j]]
-                lz = oracle.log_posterior("z", rl, I.d, rho, 1.0, I.sigma_n)
-                qz = (lz >= math.log(1 - t)).astype(float) if quantised else np.exp(lz)
-                best = None
-                for s in range(I.d):
-                    if not lz[s] <= math.log(1 - t):
-                        continue
-                    le = oracle.log_posterior("e", rl[s] - rl, I.d, rho, 1.0, I.sigma_n)
-                    qe = (le >= math.log(t)).astype(float) if quantised else np.exp(le)
-                    ne, nzv = qe.sum(), qz.sum()
-                    w = (rl * qe).sum() / ne
-                    if np.abs(rl - w).sum() <= np.abs(rl).sum() and ne - nzv >= alpha:
-                        if best is None or ne - nzv > best[0]:
-                            best = (ne - nzv, w)
-                if best is not None:
-                    xp[j] = xh[j] + best[1]
-            nz = np.nonzero(xp)[0]
-            keep = nz[np.lexsort((nz, -np.abs(xp[nz])))][:I.k]
-            xk = np.zeros_like(xp)
-            xk[keep] = xp[keep]
-            np.testing.assert_allclose(xp_c, xk, rtol=1e-12, atol=1e-14)
-            np.testing.assert_allclose(rp_c, y - A @ xk, rtol=0, atol=1e-12)
+        xh0, _, _ = oracle.decode(I.rows, y, I.k, sigma_n=I.sigma_n, quantised=quantised, max_rounds=2)
+        states = [(xh0, y - A @ xh0)] + _perturbed_states(I, y, rng)
+        for xh, rh in states:
+            for ridx in (1, 4, 8):
+                t = 1 - ridx * c
+                xp_c, rp_c, upd, rec = oracle.round_step(I.rows, y, I.k, ridx, xh, rh, sigma_n=I.sigma_n,
+                                                         quantised=quantised)
+                total_upd += upd
+                xk = _python_round(I, y, xh, rh, t, quantised, alpha)
+                np.testing.assert_allclose(xp_c, xk, rtol=1e-12, atol=1e-14)
+                np.testing.assert_allclose(rp_c, y - A @ xk, rtol=0, atol=1e-12)
+    assert total_upd > 50
+
+
+@pytest.mark.parametrize("quantised", [False, True])
+def test_one_round_corrects_shifted_entries_back_to_the_truth(quantised):
+    # Ground truth: with x_hat = x except a few isolated support entries shifted by s_j,
+    # the rows of such a column hold -s_j plus noise, the consensus is -s_j, and the
+    # round returns x'_j = x_hat_j + w close to x_j (within a few noise std).
+    n, m, k, d, sn = 4096, 1024, 24, 7, 1e-3
+    I, y = _instance(dict(n=n, m=m, k=k, d=d, sigma_n=sn), 9, f32=False)
+    A = _A(I.rows, m)
+    rng = np.random.default_rng(3)
+    supp = I.support
+    # isolated: no row shared with any other support column
+    cnt = np.bincount(I.rows[supp].ravel(), minlength=m)
+    iso = [j for j in supp if np.all(cnt[I.rows[j]] == 1)]
+    assert len(iso) >= 6
+    sh = np.array(iso[:6])
+    xh = I.x.astype(np.float64).copy()
+    xh[sh] += rng.choice([-1, 1], sh.size) * rng.uniform(0.3, 1.0, sh.size)
+    c = oracle.default_c(quantised, m / n, k / m)
+    xp, rp, upd, rec = oracle.round_step(I.rows, y, k, int(round(0.5 / c)), xh, y - A @ xh,
+                                         sigma_n=sn, quantised=quantised)
+    np.testing.assert_allclose(xp[sh], I.x[sh], atol=6 * sn)
+    others = np.setdiff1d(np.arange(n), sh)
+    assert np.count_nonzero(xp[others] != xh[others]) <= 2
