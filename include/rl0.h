@@ -1,0 +1,169 @@
+/*
+ * rl0.h -- C ABI of the GB300 (sm_103a) Robust-l0 decoding library.
+ *
+ * Robust-l0 (Mendoza-Smith, Tanner, Wechsung, arXiv 1704.09012, Algorithm 2)
+ * recovers a k-sparse x in R^n from a noisy expander sketch y_hat = A x + eta,
+ * where A in {0,1}^{m x n} has exactly d ones per column (Def. 1.1, expander
+ * matrices) and the instance follows the generating model GM(n,m,k,d,mu,nu)
+ * (Def. "Generating model") with mu = N(0, sigma_s^2) and nu = N(0, sigma_n^2).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: RL0_OK (0) on success, a negative RL0_ERR_* code otherwise;
+ *    rl0_strerror() gives a message.  Failing to converge is not an error: it
+ *    is reported in rl0_stats.converged.
+ *  - "device" pointers are CUDA device memory of the current device, owned by
+ *    the caller; "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is ordered on that stream.  Calls that return
+ *    statistics (rl0_decode*, rl0_round_step) synchronise the stream before
+ *    returning; the others only enqueue work.
+ *  - Element types: rows int32, values float (IEEE binary32), sizes int64.
+ *  - An rl0_expander owns its device copies of A and a decode workspace.  It
+ *    serves one decode at a time: calls that use the same expander must be
+ *    ordered (same stream, or synchronised), or they race on the workspace.
+ *  - No entry point falls back to the CPU: without a usable CUDA device every
+ *    call that needs one returns RL0_ERR_CUDA.
+ */
+#ifndef RL0_H
+#define RL0_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RL0_OK                 0
+#define RL0_ERR_INVALID_ARG   -1   /* a size, pointer or parameter is out of range   */
+#define RL0_ERR_CUDA          -2   /* a CUDA runtime call failed                      */
+#define RL0_ERR_ALLOC         -3   /* device or host allocation failed                */
+#define RL0_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up              */
+#define RL0_ERR_UNSUPPORTED   -5   /* valid request this build does not implement    */
+#define RL0_ERR_INVALID_A     -6   /* rows out of range, duplicated or unsorted       */
+#define RL0_ERR_INVALID_Y     -7   /* y_hat holds NaN or Inf                          */
+
+/* Opaque handle: device copy of A as column-major row lists (column j owns
+ * rows[j*d .. j*d+d-1], ascending), its transpose in CSR form, and the decode
+ * workspace sized for (n, m, d). */
+typedef struct rl0_expander rl0_expander;
+
+/* Decoder parameters (Algorithm 2's inputs besides A, y_hat and k).
+ * Zero in a field selects the documented default. */
+typedef struct {
+    double sigma_s;        /* std of the nonzeros of x (mu); 0 = 1.0                          */
+    double sigma_n;        /* std of the noise (nu); 0 = noiseless                            */
+    int    quantised;      /* Table "scores": 1 = quantised scores, 0 = continuous            */
+    int    adaptive_k;     /* the adaptive_k flag of Algorithm 2; must be 0                   */
+    double c;              /* sweep step of t; 0 = Eqs. (finetune_c_quant)/(finetune_c_cont)  */
+    double alpha;          /* consensus threshold on n_e - n_z; 0 = floor(d/2)+1 (quantised)  */
+                           /* or d/2 (continuous)                                            */
+    int    ell;            /* explicit terms of the posterior series, Eq. (pz_approx); 0 = 4  */
+    int    scorer;         /* 0 = analytic scores (Algorithm 2), 1 = learned column scorer    */
+    const void *mlp;       /* scorer = 1: device pointer to an rl0_mlp_weights block          */
+    double mlp_threshold;  /* scorer = 1: accept a column when its score >= this; 0 = 0.5     */
+    int    max_rounds;     /* cap on the number of rounds; 0 = every round with t > 0         */
+    double noiseless_tol;  /* sigma_n = 0: |a - b| <= tol counts as equal; 0 = 1e-5           */
+} rl0_params;
+
+/* Per-decode statistics (host structure filled by the library). */
+typedef struct {
+    int     rounds;            /* rounds executed (including t = 1)                          */
+    int     accepted_rounds;   /* rounds whose candidate passed ||r||_1 < ||r_hat||_1        */
+    int     converged;         /* 1 if ||r_hat||_1 <= m sigma_n sqrt(2/pi) at exit           */
+    int     status;            /* RL0_OK, or the device-side error of this decode            */
+    int64_t support_size;      /* |supp x_hat|                                               */
+    double  final_l1;          /* ||y_hat - A x_hat||_1, recomputed in FP64 at exit          */
+    float   ms;                /* device time of the decode (CUDA events), milliseconds      */
+    int     hk_rounds;         /* rounds in which H_k had to drop entries                    */
+    int     fallback_rounds;   /* rounds whose residual took the full CSR rebuild            */
+} rl0_stats;
+
+/* Def. "Generating model", item 1: draw A with each column's support uniform
+ * over the d-subsets of [m].  Counter-based: column j's rows come from
+ * Philox4x32-10 (key = seed, counter = (block, j_lo, j_hi, 0x41)), words
+ * mapped to [0, m) by Lemire's unbiased multiply-shift, duplicates skipped,
+ * then sorted.  Requires 1 <= d <= 32, d <= m < 2^31, 1 <= n, n*d < 2^31.
+ * On success *out owns new device memory; free it with rl0_free_expander. */
+int rl0_make_expander(int64_t n, int64_t m, int d, uint64_t seed,
+                      void *cuda_stream, rl0_expander **out);
+
+/* Same, from caller-supplied column-major rows (device, n*d int32, each column
+ * ascending and distinct, values in [0, m)).  The rows are copied and
+ * validated on the device; bad rows give RL0_ERR_INVALID_A. */
+int rl0_expander_from_rows(int64_t n, int64_t m, int d, const int32_t *rows_dev,
+                           void *cuda_stream, rl0_expander **out);
+
+/* Copy the expander's column-major rows (n*d int32) into rows_dev. */
+int rl0_expander_rows(const rl0_expander *A, int32_t *rows_dev, void *cuda_stream);
+
+/* Sizes of an expander (any out pointer may be NULL). */
+int rl0_expander_shape(const rl0_expander *A, int64_t *n, int64_t *m, int *d);
+
+void rl0_free_expander(rl0_expander *A);
+
+/* Def. "Generating model", items 4 and 6: y_hat = A x + eta.
+ * x_dev: device float[n]; y_dev: device float[m] (output, overwritten).
+ * y_i sums x over the row's columns in ascending column order in FP64 and adds
+ * eta_i = sigma_n * z_i, z_i a Box-Muller deviate of one Philox4x32-10 block
+ * (key = noise_seed, counter = (0, i_lo, i_hi, 0x4E)); the sum is rounded to
+ * FP32 once.  sigma_n = 0 gives the noiseless sketch. */
+int rl0_sketch(const rl0_expander *A, const float *x_dev, double sigma_n, uint64_t noise_seed,
+               float *y_dev, void *cuda_stream);
+
+/* Algorithm 2 (Robust-l0), non-adaptive, on one instance.
+ * y_dev: device float[m]; xhat_dev: device float[n] (output, overwritten).
+ * k in [1, n].  params may be NULL (all defaults with sigma_n = 0).
+ * stats (host, may be NULL) is filled after the stream is synchronised. */
+int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
+               float *xhat_dev, rl0_stats *stats, void *cuda_stream);
+
+/* rl0_decode with host buffers: copies y_host (float[m]) to the device and
+ * x_hat back to xhat_host (float[n]) on the stream.  Pinned host memory gives
+ * asynchronous copies; pageable memory works too. */
+int rl0_decode_host(const rl0_expander *A, const float *y_host, int64_t k,
+                    const rl0_params *params, float *xhat_host, rl0_stats *stats,
+                    void *cuda_stream);
+
+/* One round of Algorithm 2 from an injected state, for tests and tools:
+ * reads x_hat (xhat_dev, float[n]) and r_hat (rhat_dev, float[m]) at sweep
+ * value t = 1 - round_index * c, writes x' = H_k(x_hat + updates) to xp_dev
+ * (float[n]) and r = y_hat - A x' to rp_dev (float[m]).  passed_dev (int32[n],
+ * may be NULL) receives 1 for every column that received an update.  l1_out
+ * (host, may be NULL) receives ||r||_1 in FP64. */
+int rl0_round_step(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
+                   int round_index, const float *xhat_dev, const float *rhat_dev,
+                   float *xp_dev, float *rp_dev, int32_t *passed_dev, double *l1_out,
+                   void *cuda_stream);
+
+/* Algorithm 2 on `count` independent instances in one persistent launch
+ * (instances may differ in n, m, k, d <= 32 and parameters).  A, y_dev,
+ * xhat_dev and k point to `count` entries each (host arrays of device
+ * pointers); params points to `count` entries or is NULL; stats (host) to
+ * `count` entries or NULL.  Each instance's result equals what rl0_decode
+ * gives for it alone. */
+int rl0_decode_batched(int count, const rl0_expander *const *A, const float *const *y_dev,
+                       const int64_t *k, const rl0_params *params, float *const *xhat_dev,
+                       rl0_stats *stats, void *cuda_stream);
+
+/* Per-round record of the last rl0_decode on this expander (host copy kept by
+ * the library).  Writes min(cap, rounds) records and returns the number of
+ * rounds of that decode. */
+typedef struct {
+    double t;              /* sweep value of the round                         */
+    double l1_candidate;   /* ||y_hat - A x'||_1 of the round's candidate       */
+    double l1_hat;         /* ||r_hat||_1 after the round                       */
+    int    accepted;       /* candidate kept (||r||_1 < ||r_hat||_1)            */
+    int    updated;        /* columns that received an update                   */
+    int    support;        /* |supp x_hat| after the round                       */
+    int    hk_dropped;     /* entries H_k zeroed                                 */
+} rl0_round_record;
+
+int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap);
+
+const char *rl0_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RL0_H */

@@ -1,0 +1,142 @@
+// rl0_common.cuh -- internal declarations shared by the CUDA translation units of
+// the Robust-l0 library (arXiv 1704.09012, Algorithm 2).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rl0.h"
+
+#define RL0_MAXQ 12          // explicit series terms + tail (ell <= 10)
+#define RL0_BUCKET 8         // contributors per row held by the sparse rebuild
+#define RL0_ROWS_CHUNK 1024  // rows per l1 partial (fixed: defines the summation order)
+#define RL0_MAX_D 32
+
+// Status codes a kernel can leave in DecodeState::status.
+#define RL0_DEV_OK 0
+#define RL0_DEV_TIMEOUT 1
+
+// 1/p_breve(w) = sum_q a[q] exp(b[q] w^2), q = 0..nq-1 (Eq. (pz_approx) or
+// (pe_approx) divided through by the noise density, Eq. (breve) normalisation);
+// beyond |w| > cut the posterior is below 2^-40 and is taken as 0.
+struct Series {
+    int nq;
+    float a[RL0_MAXQ];
+    float b[RL0_MAXQ];
+    float cut;
+};
+
+// Per-round thresholds on magnitudes, FP64-derived and rounded outward so that
+// comparing an FP32 value with them is the exact test on that value:
+//   anchor  (1 - p_z(r) >= t)   <=> |r| >= ta
+//   q_z = 1 (quantised/noiseless)<=> |r| <= tz
+//   q_e = 1 (quantised/noiseless)<=> |D| <= te
+struct RoundThr {
+    float ta, tz, te, t;
+};
+
+struct RoundLog {
+    double l1_candidate;
+    double l1_hat;
+    int accepted;
+    int updated;
+    int support;
+    int hk_dropped;
+};
+
+// Mutable state of one decode, in device memory.
+struct DecodeState {
+    int done;
+    int status;
+    int round;
+    int cur;                  // which rz buffer holds r_hat
+    unsigned shat_count;      // |supp x_hat|: list[0 .. shat_count) is the support
+    unsigned list_count;      // support + columns that became nonzero this round
+    unsigned upd_count;       // updates this round (undo log length)
+    unsigned drop_count;      // entries H_k zeroed this round (undo log length)
+    int overflow;             // a row had more than RL0_BUCKET contributors
+    int converged;            // ||r_hat||_1 <= stop level
+    int rounds_run;
+    int accepted_rounds;
+    int hk_rounds;
+    int fallback_rounds;
+    double l1_hat;
+    double l1_new;
+};
+
+// Per-call data the round kernels read from device memory.  The graph that
+// replays the round loop captures only the address of this block, so one
+// captured graph serves every call on the same expander.
+struct DecodeCtx {
+    const float *y;           // y_hat, float[m]
+    float *x;                 // the working x (x_hat, updated in place), float[n]
+    long long k;
+    float alpha;
+    int nrounds;
+    int quantised;
+    int indicator;            // quantised or noiseless: 0/1 scores
+    double stop_level;        // absolute stop level (sigma_n > 0)
+    double stop_rel;          // > 0: stop level = stop_rel * ||y_hat||_1 (noiseless)
+    Series pz, pe;
+    int scorer;               // 0 analytic, 1 learned
+    const void *mlp;
+    float mlp_threshold;
+    int32_t *passed;          // optional per-column pass flags (round_step)
+    int want_log;
+};
+
+struct UndoEntry {
+    int j;
+    float old;
+};
+
+// Device workspace owned by an expander.
+struct Workspace {
+    float2 *rz[2];            // (r_i, p_z(r_i)) for r_hat and the candidate r
+    int *list;                // support + new nonzeros, capacity n
+    int *list_tmp;            // compaction scratch, capacity n
+    UndoEntry *ulog;          // updates of this round, capacity n
+    UndoEntry *dlog;          // H_k drops of this round, capacity n
+    int *bcnt;                // per-row contributor counts, int[m] (kept zero between rounds)
+    int *bkt;                 // per-row contributor columns, int[m * RL0_BUCKET]
+    double *l1part;           // per-chunk l1 partials
+    unsigned long long *hk_scratch;  // H_k candidate keys, capacity n
+    DecodeState *st;
+    DecodeCtx *ctx;
+    RoundThr *thr;            // per-round thresholds, capacity RL0_MAX_ROUNDS
+    RoundLog *rlog;           // per-round log, capacity RL0_MAX_ROUNDS
+    double *final_part;       // FP64 final-residual partials
+    int max_rounds;
+};
+
+struct rl0_expander {
+    int64_t n, m;
+    int d;
+    int device;
+    int32_t *rows_cm;         // column-major rows, int[n*d]
+    int32_t *rows_sm;         // slot-major rows: rows_sm[s*n + j], int[d*n]
+    int32_t *rowptr;          // CSR of A^T: int[m+1]
+    int32_t *colidx;          // CSR of A^T: int[n*d], ascending within a row
+    Workspace ws;
+    void *graph_cache;        // captured round loops
+    void *host_pinned;        // pinned staging (ctx, thresholds, stats)
+    size_t host_pinned_bytes;
+    int *dev_flag;            // validation flag
+    int last_log_rounds;      // rounds recorded by the last rl0_decode
+};
+
+#define RL0_MAX_ROUNDS 1024
+
+// ---- helpers shared by translation units -------------------------------
+int rl0_set_device_of(const rl0_expander *A);
+int rl0_cuda_err(cudaError_t e);
+
+// Expander construction pieces (rl0_expander.cu).
+int rl0_expander_finish(rl0_expander *A, cudaStream_t s);
+void rl0_expander_release(rl0_expander *A);
+
+// Decode workspace (rl0_decode.cu).
+int rl0_workspace_alloc(rl0_expander *A);
+void rl0_workspace_free(rl0_expander *A);
+
+static inline unsigned rl0_div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

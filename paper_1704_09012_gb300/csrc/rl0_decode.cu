@@ -1,0 +1,1112 @@
+// rl0_decode.cu -- the synchronous round loop of Robust-l0 (arXiv 1704.09012,
+// Algorithm 2) on one instance: per-round thresholds and posterior
+// coefficients (host, FP64), the round kernels, and the captured CUDA graph
+// that replays the loop.
+//
+// One round, as kernels on one stream:
+//   column_score  every column j reads its d residuals (slot-major row ids,
+//                 one coalesced 4-byte load per slot per thread, L2 gathers of
+//                 (r, p_z(r))), scores every anchor (Table "scores",
+//                 Eqs. (ne_nz_1), (ne_nz_2)), applies the best passing update
+//                 to x in place and logs it for undo;
+//   hk_select     H_k on the list of nonzeros (single CTA radix select on the
+//                 63-bit key (|x_j| bits, ~j): ties go to the smaller j);
+//   scatter       the support's (row, column) pairs into per-row buckets;
+//   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32, with
+//                 p_z(r_i) and FP64 l1 partials over fixed 1024-row chunks
+//                 (a CSR(A^T) pass replaces it when a bucket overflows);
+//   accept        ||r||_1 < ||r_hat||_1 keeps the round, otherwise undoes it;
+//                 advances t and sets the done flag (converged or t <= 0).
+// No float atomics anywhere: every sum has a fixed order, so results do not
+// depend on the launch configuration or on scheduling.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rl0_common.cuh"
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return rl0_cuda_err(e_);   \
+    } while (0)
+
+// Fixed pointers and sizes of one expander's decode, passed by value.
+struct KArgs {
+    int n, m, d, nchunks, nsm;
+    const int32_t *rows_sm, *rows_cm, *rowptr, *colidx;
+    float2 *rz0, *rz1;
+    int *list;
+    UndoEntry *ulog, *dlog;
+    int *bcnt, *bkt;
+    double *l1part;
+    unsigned long long *hkkey;
+    DecodeState *st;
+    DecodeCtx *ctx;
+    const RoundThr *thr;
+    RoundLog *rlog;
+    double *final_part;
+};
+
+// ---------------------------------------------------------------------------
+// Posterior evaluation in FP32: 1/p_breve(w) = sum_q a_q exp(b_q w^2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float series_eval(const Series &S, float w)
+{
+    if (w == 0.0f) return 1.0f;                 // p_breve(0) = 1 exactly
+    if (fabsf(w) > S.cut) return 0.0f;          // below 2^-40
+    const float w2 = w * w;
+    float acc = S.a[0];
+    for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * w2);
+    return 1.0f / acc;
+}
+
+__device__ __forceinline__ double block_sum_f64(double v, double *sh)
+{
+    // fixed-shape tree over the block: deterministic for a given blockDim
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
+        if (t < off) sh[t] += sh[t + off];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each 1024-row chunk.
+// 256 threads per chunk, thread t handles rows t, t+256, t+512, t+768.
+__global__ void __launch_bounds__(256) k_rows_from(KArgs a, const float *src_override, int dst)
+{
+    __shared__ double sh[256];
+    const DecodeCtx *ctx = a.ctx;
+    const float *src = src_override ? src_override : ctx->y;
+    float2 *rz = dst ? a.rz1 : a.rz0;
+    const bool smooth = !ctx->indicator;
+    double l1 = 0.0;
+    bool bad = false;
+    const int base = blockIdx.x * RL0_ROWS_CHUNK;
+    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
+        const int i = base + u * 256 + threadIdx.x;
+        if (i < a.m) {
+            const float r = src[i];
+            bad |= !isfinite(r);
+            const float z = smooth ? series_eval(ctx->pz, r) : 0.0f;
+            rz[i] = make_float2(r, z);
+            l1 += fabs((double)r);
+        }
+    }
+    if (bad) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
+    const double s = block_sum_f64(l1, sh);
+    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+}
+
+// Zero the working x.
+__global__ void k_zero_x(KArgs a)
+{
+    float *x = a.ctx->x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x) x[j] = 0.0f;
+}
+
+// Initial state: r_hat = the source, ||r_hat||_1 from the chunk partials in order.
+__global__ void k_start(KArgs a, int round0, int empty_support)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    DecodeState *st = a.st;
+    double l1 = 0.0;
+    for (int c = 0; c < a.nchunks; ++c) l1 += a.l1part[c];
+    const int status = st->status;
+    st->round = round0;
+    st->cur = 0;
+    if (empty_support) { st->shat_count = 0; st->list_count = 0; }
+    st->upd_count = 0;
+    st->drop_count = 0;
+    st->overflow = 0;
+    st->rounds_run = 0;
+    st->accepted_rounds = 0;
+    st->hk_rounds = 0;
+    st->fallback_rounds = 0;
+    st->l1_hat = l1;
+    st->l1_new = l1;
+    double stop = a.ctx->stop_level;
+    if (a.ctx->stop_rel > 0.0) stop = a.ctx->stop_rel * l1;
+    a.ctx->stop_level = stop;
+    st->converged = (l1 <= stop);
+    st->done = (status != 0) || st->converged || (round0 >= a.ctx->nrounds);
+}
+
+// Support list of an injected x_hat (order irrelevant: every consumer sorts
+// or selects by key).
+__global__ void k_support_from_x(KArgs a)
+{
+    const float *x = a.ctx->x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool nz = (j < a.n) && x[j] != 0.0f;
+    const unsigned mask = __ballot_sync(0xffffffffu, nz);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&a.st->shat_count, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (nz) a.list[base + __popc(mask & ((1u << lane) - 1u))] = j;
+}
+
+__global__ void k_list_count_from_support(KArgs a)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) a.st->list_count = a.st->shat_count;
+}
+
+// ---------------------------------------------------------------------------
+// Column score: Algorithm 2's loop over j in [n] and i in N(j).
+// ---------------------------------------------------------------------------
+template <int DMAX, bool IND>
+__global__ void __launch_bounds__(256) k_column_score(KArgs a)
+{
+    __shared__ Series s_pe;
+    const DecodeState *st = a.st;
+    if (st->done) return;
+    const DecodeCtx *ctx = a.ctx;
+    const int round = st->round;
+    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
+    const RoundThr th = a.thr[round];
+    const float alpha = ctx->alpha;
+    if (!IND) {
+        if (threadIdx.x == 0) s_pe = ctx->pe;
+        __syncthreads();
+    }
+    const int n = a.n, d = a.d;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = j < n;
+
+    float r[DMAX], z[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        r[s] = 0.0f;
+        z[s] = 0.0f;
+        if (s < d && active) {
+            const int row = __ldg(a.rows_sm + (size_t)s * n + j);
+            const float2 v = __ldg(rz + row);
+            r[s] = v.x;
+            z[s] = v.y;
+        }
+    }
+    float nz = 0.0f, rhs = 0.0f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        if (s < d) {
+            nz += IND ? (fabsf(r[s]) <= th.tz ? 1.0f : 0.0f) : z[s];
+            rhs += fabsf(r[s]);
+        }
+    }
+    int best = -1;
+    float bscore = 0.0f, bw = 0.0f;
+    if (active) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s >= d || !(fabsf(r[s]) >= th.ta)) continue;     // anchor: 1 - p_z(r_i) >= t
+            float ne = 0.0f, num = 0.0f;
+            if (IND) {
+#pragma unroll
+                for (int l = 0; l < DMAX; ++l) {
+                    if (l < d) {
+                        const float q = (fabsf(r[s] - r[l]) <= th.te) ? 1.0f : 0.0f;
+                        ne += q;
+                        num += r[l] * q;
+                    }
+                }
+            } else {
+                // n_e <= 1 + #{l != i : |r_i - r_l| <= cut}: skip anchors that cannot pass
+                int near = 0;
+#pragma unroll
+                for (int l = 0; l < DMAX; ++l)
+                    if (l < d && l != s && fabsf(r[s] - r[l]) <= s_pe.cut) ++near;
+                if ((1.0f + (float)near) - nz < alpha - 1e-3f) continue;
+#pragma unroll
+                for (int l = 0; l < DMAX; ++l) {
+                    if (l < d) {
+                        const float q = series_eval(s_pe, r[s] - r[l]);
+                        ne += q;
+                        num += r[l] * q;
+                    }
+                }
+            }
+            const float w = num / ne;
+            float lhs = 0.0f;
+#pragma unroll
+            for (int l = 0; l < DMAX; ++l)
+                if (l < d) lhs += fabsf(r[l] - w);
+            const float score = ne - nz;
+            if (lhs <= rhs && score >= alpha && (best < 0 || score > bscore)) {
+                best = s;
+                bscore = score;
+                bw = w;
+            }
+        }
+    }
+    const bool pass = best >= 0;
+    float old = 0.0f, nv = 0.0f;
+    if (pass) {
+        float *x = ctx->x;
+        old = x[j];
+        nv = old + bw;
+        x[j] = nv;
+    }
+    if (ctx->passed && active) ctx->passed[j] = pass ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    unsigned mask = __ballot_sync(0xffffffffu, pass);
+    if (mask) {
+        const int leader = __ffs(mask) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(&a.st->upd_count, (unsigned)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (pass) {
+            UndoEntry e;
+            e.j = j;
+            e.old = old;
+            a.ulog[base + __popc(mask & ((1u << lane) - 1u))] = e;
+        }
+        const bool fresh = pass && old == 0.0f && nv != 0.0f;
+        mask = __ballot_sync(0xffffffffu, fresh);
+        if (mask) {
+            const int ld2 = __ffs(mask) - 1;
+            if (lane == ld2) base = atomicAdd(&a.st->list_count, (unsigned)__popc(mask));
+            base = __shfl_sync(0xffffffffu, base, ld2);
+            if (fresh) a.list[base + __popc(mask & ((1u << lane) - 1u))] = j;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// H_k: keep the k entries of largest |x'_j| (ties -> smaller j); single CTA.
+// Radix select of the k-th largest 63-bit key (bits(|x|) << 32 | ~j) in six
+// passes of at most 11 bits, then zero (and log) everything below it.
+// ---------------------------------------------------------------------------
+#define HK_THREADS 1024
+#define HK_BINS 2048
+
+__device__ __forceinline__ unsigned long long hk_key(float v, int j)
+{
+    return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (unsigned long long)(0xffffffffu - (unsigned)j);
+}
+
+__global__ void __launch_bounds__(HK_THREADS) k_hk_select(KArgs a)
+{
+    __shared__ unsigned hist[HK_BINS];
+    __shared__ unsigned suf[HK_THREADS];
+    __shared__ unsigned s_red[32];
+    __shared__ unsigned long long s_prefix;
+    __shared__ unsigned s_need;
+    DecodeState *st = a.st;
+    if (st->done || st->upd_count == 0) return;
+    const long long k = a.ctx->k;
+    const float *x = a.ctx->x;
+    const unsigned total = st->list_count;
+    const int t = threadIdx.x;
+
+    // keys of the nonzero entries; count them
+    unsigned cnt = 0;
+    for (unsigned e = t; e < total; e += HK_THREADS) {
+        const int j = a.list[e];
+        const float v = x[j];
+        const unsigned long long key = (v != 0.0f) ? hk_key(v, j) : 0ull;
+        a.hkkey[e] = key;
+        cnt += (v != 0.0f);
+    }
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    if ((t & 31) == 0) s_red[t >> 5] = cnt;
+    __syncthreads();
+    if (t < 32) {
+        unsigned v = s_red[t];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (t == 0) s_red[0] = v;
+    }
+    __syncthreads();
+    const unsigned nnz = s_red[0];
+    if ((long long)nnz <= k) return;
+
+    if (t == 0) { s_prefix = 0ull; s_need = (unsigned)k; }
+    __syncthreads();
+    const int shifts[6] = {52, 41, 30, 19, 8, 0};
+    const int widths[6] = {11, 11, 11, 11, 11, 8};
+    for (int p = 0; p < 6; ++p) {
+        const int sh = shifts[p], wd = widths[p];
+        const unsigned nb = 1u << wd;
+        for (unsigned b = t; b < HK_BINS; b += HK_THREADS) hist[b] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix;
+        const unsigned need = s_need;
+        for (unsigned e = t; e < total; e += HK_THREADS) {
+            const unsigned long long key = a.hkkey[e];
+            if (key != 0ull && (key >> (sh + wd)) == prefix)
+                atomicAdd(&hist[(unsigned)(key >> sh) & (nb - 1u)], 1u);
+        }
+        __syncthreads();
+        // inclusive suffix sums over bins, two bins per thread (high bins first)
+        const unsigned b0 = nb - 1 - 2 * t, b1 = b0 - 1;
+        const unsigned own = (2u * t < nb) ? hist[b0] + (2u * t + 1 < nb ? hist[b1] : 0u) : 0u;
+        suf[t] = own;
+        __syncthreads();
+        for (int off = 1; off < HK_THREADS; off <<= 1) {
+            const unsigned v = (t >= off) ? suf[t - off] : 0u;
+            __syncthreads();
+            suf[t] += v;
+            __syncthreads();
+        }
+        if (2u * t < nb) {
+            const unsigned before = suf[t] - own;           // count in bins above b0
+            const unsigned at_b0 = before + hist[b0];
+            if (before < need && at_b0 >= need) {
+                s_prefix = (prefix << wd) | b0;
+                s_need = need - before;
+            } else if (2u * t + 1 < nb && at_b0 < need && suf[t] >= need) {
+                s_prefix = (prefix << wd) | b1;
+                s_need = need - at_b0;
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long kth = s_prefix;            // the k-th largest key
+    for (unsigned e = t; e < total; e += HK_THREADS) {
+        const unsigned long long key = a.hkkey[e];
+        if (key != 0ull && key < kth) {
+            const int j = a.list[e];
+            float *xm = a.ctx->x;
+            UndoEntry u;
+            u.j = j;
+            u.old = xm[j];
+            xm[j] = 0.0f;
+            a.dlog[atomicAdd(&st->drop_count, 1u)] = u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual rebuild r = y - A x'.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scatter(KArgs a)
+{
+    DecodeState *st = a.st;
+    if (st->done || st->upd_count == 0) return;
+    const float *x = a.ctx->x;
+    const unsigned total = st->list_count;
+    const int d = a.d;
+    const long long work = (long long)total * d;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < work;
+         w += (long long)gridDim.x * blockDim.x) {
+        const unsigned e = (unsigned)(w / d);
+        const int s = (int)(w % d);
+        const int j = a.list[e];
+        if (x[j] == 0.0f) continue;
+        const int row = a.rows_cm[(long long)j * d + s];
+        const int slot = atomicAdd(&a.bcnt[row], 1);
+        if (slot < RL0_BUCKET) a.bkt[(long long)row * RL0_BUCKET + slot] = j;
+        else a.st->overflow = 1;
+    }
+}
+
+template <bool CSR>
+__global__ void __launch_bounds__(256) k_rebuild(KArgs a)
+{
+    __shared__ double sh[256];
+    DecodeState *st = a.st;
+    if (st->done || st->upd_count == 0) return;
+    if ((st->overflow != 0) != CSR) return;
+    const DecodeCtx *ctx = a.ctx;
+    const float *x = ctx->x;
+    const float *y = ctx->y;
+    float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
+    const bool smooth = !ctx->indicator;
+    double l1 = 0.0;
+    const int base = blockIdx.x * RL0_ROWS_CHUNK;
+    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
+        const int i = base + u * 256 + threadIdx.x;
+        if (i >= a.m) continue;
+        float sum = 0.0f;
+        if (CSR) {
+            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
+            a.bcnt[i] = 0;
+        } else {
+            const int c = a.bcnt[i];
+            if (c > 0) {
+                int js[RL0_BUCKET];
+#pragma unroll
+                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
+#pragma unroll
+                for (int q = 1; q < RL0_BUCKET; ++q) {          // ascending column order
+                    const int v = js[q];
+                    int p = q - 1;
+                    while (p >= 0 && js[p] > v) { js[p + 1] = js[p]; --p; }
+                    js[p + 1] = v;
+                }
+                for (int q = 0; q < c; ++q) sum += x[js[q]];
+                a.bcnt[i] = 0;
+            }
+        }
+        const float r = y[i] - sum;
+        const float z = smooth ? series_eval(ctx->pz, r) : 0.0f;
+        rz[i] = make_float2(r, z);
+        l1 += fabs((double)r);
+    }
+    const double s = block_sum_f64(l1, sh);
+    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Accept / undo and round control (single CTA).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_accept(KArgs a)
+{
+    __shared__ double shd[1024];
+    __shared__ unsigned shu[1024];
+    __shared__ int s_acc;
+    DecodeState *st = a.st;
+    if (st->done) return;
+    const int t = threadIdx.x;
+    const unsigned upd = st->upd_count;
+    const DecodeCtx *ctx = a.ctx;
+    float *x = ctx->x;
+    double l1n = st->l1_hat;
+    if (upd > 0) {
+        double v = 0.0;
+        for (int c = t; c < a.nchunks; c += 1024) v += a.l1part[c];
+        l1n = block_sum_f64(v, shd);
+        if (t == 0) s_acc = (l1n < st->l1_hat);
+        __syncthreads();
+        if (s_acc) {
+            // stable in-place compaction of the list to the new support
+            const unsigned total = st->list_count;
+            unsigned out = 0;
+            for (unsigned base = 0; base < total; base += 1024) {
+                const unsigned e = base + t;
+                int j = -1;
+                unsigned keep = 0;
+                if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
+                shu[t] = keep;
+                __syncthreads();
+                for (int off = 1; off < 1024; off <<= 1) {
+                    const unsigned w = (t >= off) ? shu[t - off] : 0u;
+                    __syncthreads();
+                    shu[t] += w;
+                    __syncthreads();
+                }
+                const unsigned incl = shu[t];
+                const unsigned blk = shu[1023];
+                __syncthreads();
+                if (keep) a.list[out + incl - 1] = j;
+                out += blk;
+                __syncthreads();
+            }
+            if (t == 0) {
+                st->shat_count = out;
+                st->list_count = out;
+                st->cur ^= 1;
+                st->l1_hat = l1n;
+                st->accepted_rounds += 1;
+            }
+        } else {
+            const unsigned nd = st->drop_count;
+            for (unsigned e = t; e < nd; e += 1024) x[a.dlog[e].j] = a.dlog[e].old;
+            __syncthreads();
+            for (unsigned e = t; e < upd; e += 1024) x[a.ulog[e].j] = a.ulog[e].old;
+            if (t == 0) st->list_count = st->shat_count;
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int round = st->round;
+        if (ctx->want_log && round < RL0_MAX_ROUNDS) {
+            RoundLog L;
+            L.l1_candidate = l1n;
+            L.l1_hat = st->l1_hat;
+            L.accepted = (upd > 0) ? s_acc : 0;
+            L.updated = (int)upd;
+            L.support = (int)st->shat_count;
+            L.hk_dropped = (int)st->drop_count;
+            a.rlog[round] = L;
+        }
+        if (upd > 0 && st->drop_count > 0) st->hk_rounds += 1;
+        if (upd > 0 && st->overflow) st->fallback_rounds += 1;
+        st->upd_count = 0;
+        st->drop_count = 0;
+        st->overflow = 0;
+        st->round = round + 1;
+        st->rounds_run += 1;
+        st->l1_new = l1n;
+        st->converged = (st->l1_hat <= ctx->stop_level);
+        if (st->converged || st->round >= ctx->nrounds) st->done = 1;
+    }
+}
+
+// ||y - A x_hat||_1 with every step in FP64 (the final residual-norm check).
+__global__ void __launch_bounds__(256) k_final_l1(KArgs a)
+{
+    __shared__ double sh[256];
+    const float *x = a.ctx->x;
+    const float *y = a.ctx->y;
+    double l1 = 0.0;
+    const int base = blockIdx.x * RL0_ROWS_CHUNK;
+    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
+        const int i = base + u * 256 + threadIdx.x;
+        if (i >= a.m) continue;
+        double acc = (double)y[i];
+        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) acc -= (double)x[a.colidx[p]];
+        l1 += fabs(acc);
+    }
+    const double s = block_sum_f64(l1, sh);
+    if (threadIdx.x == 0) a.final_part[blockIdx.x] = s;
+}
+
+// round_step output: the candidate residual (or r_hat when nothing changed).
+__global__ void k_extract_r(KArgs a, float *rp, int use_candidate_always)
+{
+    const DecodeState *st = a.st;
+    const bool changed = use_candidate_always || st->upd_count > 0;
+    const float2 *src = (st->cur ^ (changed ? 1 : 0)) ? a.rz1 : a.rz0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += gridDim.x * blockDim.x) rp[i] = src[i].x;
+}
+
+// ---------------------------------------------------------------------------
+// Host: posterior coefficients and thresholds in FP64.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HostSeries {
+    int nq;
+    double a[RL0_MAXQ], b[RL0_MAXQ];
+};
+
+// Eq. (pz_approx) (lam = d rho, vn = s_n^2) or Eq. (pe_approx) (lam = 2 d rho,
+// vn = 2 s_n^2): terms q = 0..ell with weight lam^q/q! and variance
+// q s_s^2 + vn, and the tail R(ell) = sum_{q>ell} lam^q/q! with the
+// variance-matched v = (s_s^2 lam R(ell-1) + vn R(ell)) / R(ell).  Dividing
+// numerator and denominator by the noise density gives
+//   p(0)/p(w) = sum_terms c_t sqrt(vn/v_t) exp(w^2 (1/(2 vn) - 1/(2 v_t))) / D,
+// with D the same sum at w = 0 (the maximum of p is at 0).
+HostSeries make_series(double lam, double s2, double vn, int ell)
+{
+    double wt[RL0_MAXQ], var[RL0_MAXQ];
+    int nt = 0;
+    double term = 1.0;
+    for (int q = 0; q <= ell; ++q) {
+        if (q > 0) term *= lam / q;
+        wt[nt] = term;
+        var[nt] = q * s2 + vn;
+        ++nt;
+    }
+    // tails R(ell) and R(ell - 1), summed directly
+    double tq = term, Rl = 0.0;
+    for (int q = ell + 1; q < ell + 4000; ++q) {
+        tq *= lam / q;
+        Rl += tq;
+        if (tq == 0.0 || (q > lam && tq < Rl * 1e-18)) break;
+    }
+    const double Rlm1 = Rl + term;               // adds the q = ell term
+    if (Rl > 0.0) {
+        wt[nt] = Rl;
+        var[nt] = (s2 * lam * Rlm1 + vn * Rl) / Rl;
+        ++nt;
+    }
+    HostSeries H;
+    H.nq = nt;
+    double D = 0.0;
+    for (int q = 0; q < nt; ++q) D += wt[q] * std::sqrt(vn / var[q]);
+    for (int q = 0; q < nt; ++q) {
+        H.a[q] = wt[q] * std::sqrt(vn / var[q]) / D;
+        H.b[q] = 0.5 / vn - 0.5 / var[q];
+    }
+    H.b[0] = 0.0;
+    return H;
+}
+
+double series_F(const HostSeries &H, double w)
+{
+    double acc = 0.0;
+    for (int q = 0; q < H.nq; ++q) acc += H.a[q] * std::exp(H.b[q] * w * w);
+    return acc;
+}
+
+// Smallest w >= 0 with F(w) >= T (F increasing in |w|); +inf for T = inf.
+double series_inverse(const HostSeries &H, double T)
+{
+    if (std::isinf(T)) return INFINITY;
+    if (T <= 1.0) return 0.0;
+    double lo = 0.0, hi = 1e-300;
+    for (int it = 0; it < 2200 && series_F(H, hi) < T; ++it) hi *= 2.0;
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (series_F(H, mid) >= T) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+float round_up_f(double w)
+{
+    if (std::isinf(w)) return INFINITY;
+    float f = (float)w;
+    if ((double)f < w) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+float round_down_f(double w)
+{
+    if (std::isinf(w)) return INFINITY;
+    float f = (float)w;
+    if ((double)f > w) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+// Smallest float strictly above w.
+float strictly_above_f(double w)
+{
+    float f = round_up_f(w);
+    if ((double)f == w) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+Series to_device_series(const HostSeries &H, double cut)
+{
+    Series S;
+    std::memset(&S, 0, sizeof(S));
+    S.nq = H.nq;
+    for (int q = 0; q < H.nq; ++q) { S.a[q] = (float)H.a[q]; S.b[q] = (float)H.b[q]; }
+    S.cut = round_up_f(cut);
+    return S;
+}
+
+// Eqs. (finetune_c_quant), (finetune_c_cont).
+double default_c(int quantised, double delta, double rho)
+{
+    if (quantised) {
+        if (delta <= 0.05) return 0.01;
+        if (rho <= 0.1) return 0.05;
+        if (rho <= 0.2) return 0.075;
+        return 0.1;
+    }
+    return delta <= 0.05 ? 0.01 : 0.025;
+}
+
+struct Resolved {
+    rl0_params p;
+    int nrounds;
+    int indicator;
+    double stop_level, stop_rel;
+};
+
+int resolve(const rl0_expander *A, int64_t k, const rl0_params *in, Resolved *R)
+{
+    rl0_params p;
+    std::memset(&p, 0, sizeof(p));
+    if (in) p = *in;
+    if (p.sigma_s == 0.0) p.sigma_s = 1.0;
+    if (!(p.sigma_s > 0.0) || !(p.sigma_n >= 0.0) || !std::isfinite(p.sigma_n) || !std::isfinite(p.sigma_s))
+        return RL0_ERR_INVALID_ARG;
+    if (p.adaptive_k) return RL0_ERR_UNSUPPORTED;
+    if (k < 1 || k > A->n) return RL0_ERR_INVALID_ARG;
+    if (p.c == 0.0) p.c = default_c(p.quantised, (double)A->m / (double)A->n, (double)k / (double)A->m);
+    if (!(p.c > 0.0 && p.c <= 1.0)) return RL0_ERR_INVALID_ARG;
+    if (p.alpha == 0.0) p.alpha = p.quantised ? (double)(A->d / 2 + 1) : 0.5 * A->d;
+    if (!(p.alpha > 0.0)) return RL0_ERR_INVALID_ARG;
+    if (p.ell == 0) p.ell = 4;
+    if (p.ell < 1 || p.ell > RL0_MAXQ - 2) return RL0_ERR_INVALID_ARG;
+    if (p.noiseless_tol == 0.0) p.noiseless_tol = 1e-5;
+    if (!(p.noiseless_tol > 0.0)) return RL0_ERR_INVALID_ARG;
+    if (p.scorer != 0 && p.scorer != 1) return RL0_ERR_INVALID_ARG;
+    if (p.scorer == 1) return RL0_ERR_UNSUPPORTED;
+    int nr = (int)std::ceil(1.0 / p.c - 1e-9);
+    if (p.max_rounds > 0 && p.max_rounds < nr) nr = p.max_rounds;
+    if (nr > RL0_MAX_ROUNDS) return RL0_ERR_UNSUPPORTED;
+    R->p = p;
+    R->nrounds = nr;
+    R->indicator = p.quantised || p.sigma_n == 0.0;
+    R->stop_level = (p.sigma_n > 0.0) ? (double)A->m * p.sigma_n * std::sqrt(2.0 / M_PI) : 0.0;
+    R->stop_rel = (p.sigma_n > 0.0) ? 0.0 : p.noiseless_tol;
+    return RL0_OK;
+}
+
+// Fill the device context and the per-round thresholds (host copies).
+void fill_tables(const rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr)
+{
+    const rl0_params &p = R.p;
+    const double rho = (double)k / (double)A->m;
+    const double s2 = p.sigma_s * p.sigma_s, n2 = p.sigma_n * p.sigma_n;
+    std::memset(ctx, 0, sizeof(*ctx));
+    ctx->k = k;
+    ctx->alpha = (float)p.alpha;
+    ctx->nrounds = R.nrounds;
+    ctx->quantised = p.quantised;
+    ctx->indicator = R.indicator;
+    ctx->stop_level = R.stop_level;
+    ctx->stop_rel = R.stop_rel;
+    ctx->scorer = p.scorer;
+    ctx->mlp = p.mlp;
+    ctx->mlp_threshold = (float)(p.mlp_threshold == 0.0 ? 0.5 : p.mlp_threshold);
+    HostSeries hz, he;
+    if (p.sigma_n > 0.0) {
+        hz = make_series(A->d * rho, s2, n2, p.ell);
+        he = make_series(2.0 * A->d * rho, s2, 2.0 * n2, p.ell);
+        const double tiny = std::ldexp(1.0, 40);
+        ctx->pz = to_device_series(hz, series_inverse(hz, tiny));
+        ctx->pe = to_device_series(he, series_inverse(he, tiny));
+    }
+    for (int r = 0; r < nthr; ++r) {
+        const double t = 1.0 - r * p.c;
+        RoundThr T;
+        T.t = (float)t;
+        if (p.sigma_n == 0.0) {
+            // p_breve is the indicator of |w| <= tol
+            const float tol_dn = round_down_f(p.noiseless_tol);
+            T.ta = strictly_above_f(p.noiseless_tol);       // p_z = 0  <=> |r| > tol
+            T.te = tol_dn;                                  // p_e >= t <=> |D| <= tol (t in (0, 1])
+            T.tz = (p.quantised && t >= 1.0) ? INFINITY : tol_dn;   // p_z >= 1 - t
+        } else {
+            // anchor: p_z(r) <= 1 - t <=> F_z(r) >= 1/(1-t);  q_z: p_z(r) >= 1 - t <=> F_z(r) <= 1/(1-t)
+            const double Tz = (t >= 1.0) ? INFINITY : 1.0 / (1.0 - t);
+            const double wz = series_inverse(hz, Tz);
+            T.ta = round_up_f(wz);
+            T.tz = round_down_f(wz);
+            // q_e (quantised): p_e(D) >= t <=> F_e(D) <= 1/t
+            const double we = series_inverse(he, 1.0 / t);
+            T.te = round_down_f(we);
+        }
+        thr[r] = T;
+    }
+}
+
+struct GraphEntry {
+    int nrounds, dmax, indicator;
+    cudaGraphExec_t exec;
+};
+
+struct GraphCache {
+    std::vector<GraphEntry> entries;
+    cudaStream_t capture_stream = nullptr;
+};
+
+KArgs make_args(const rl0_expander *A)
+{
+    const Workspace &w = A->ws;
+    KArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = (int)A->n;
+    a.m = (int)A->m;
+    a.d = A->d;
+    a.nchunks = (int)rl0_div_up(A->m, RL0_ROWS_CHUNK);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device);
+    a.nsm = nsm > 0 ? nsm : 1;
+    a.rows_sm = A->rows_sm;
+    a.rows_cm = A->rows_cm;
+    a.rowptr = A->rowptr;
+    a.colidx = A->colidx;
+    a.rz0 = w.rz[0];
+    a.rz1 = w.rz[1];
+    a.list = w.list;
+    a.ulog = w.ulog;
+    a.dlog = w.dlog;
+    a.bcnt = w.bcnt;
+    a.bkt = w.bkt;
+    a.l1part = w.l1part;
+    a.hkkey = w.hk_scratch;
+    a.st = w.st;
+    a.ctx = w.ctx;
+    a.thr = w.thr;
+    a.rlog = w.rlog;
+    a.final_part = w.final_part;
+    return a;
+}
+
+void launch_column_score(const KArgs &a, int dmax, int indicator, cudaStream_t s)
+{
+    const unsigned grid = rl0_div_up(a.n, 256);
+#define RL0_CS(D, I) k_column_score<D, I><<<grid, 256, 0, s>>>(a)
+    if (dmax == 8) { if (indicator) RL0_CS(8, true); else RL0_CS(8, false); }
+    else if (dmax == 16) { if (indicator) RL0_CS(16, true); else RL0_CS(16, false); }
+    else { if (indicator) RL0_CS(32, true); else RL0_CS(32, false); }
+#undef RL0_CS
+}
+
+int dmax_of(int d) { return d <= 8 ? 8 : (d <= 16 ? 16 : 32); }
+
+// The kernels of one round (shared by the graph and by round_step).
+void launch_round(const KArgs &a, int dmax, int indicator, cudaStream_t s)
+{
+    launch_column_score(a, dmax, indicator, s);
+    k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
+    k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
+    k_rebuild<false><<<a.nchunks, 256, 0, s>>>(a);
+    k_rebuild<true><<<a.nchunks, 256, 0, s>>>(a);
+}
+
+int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, cudaGraphExec_t *out)
+{
+    GraphCache *gc = (GraphCache *)A->graph_cache;
+    const KArgs a = make_args(A);
+    cudaStream_t s = gc->capture_stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
+    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, nullptr, 0);
+    k_start<<<1, 32, 0, s>>>(a, 0, 1);
+    for (int r = 0; r < nrounds; ++r) {
+        launch_round(a, dmax, indicator, s);
+        k_accept<<<1, 1024, 0, s>>>(a);
+    }
+    k_final_l1<<<a.nchunks, 256, 0, s>>>(a);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return rl0_cuda_err(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return rl0_cuda_err(e);
+}
+
+// Pinned host staging: ctx, thresholds, state, final partials, log.
+struct HostStage {
+    DecodeCtx ctx;
+    DecodeState st;
+    RoundThr thr[RL0_MAX_ROUNDS];
+    RoundLog log[RL0_MAX_ROUNDS];
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+int rl0_workspace_alloc(rl0_expander *A)
+{
+    Workspace &w = A->ws;
+    const size_t n = (size_t)A->n, m = (size_t)A->m;
+    const size_t nchunks = rl0_div_up(A->m, RL0_ROWS_CHUNK);
+    w.max_rounds = RL0_MAX_ROUNDS;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    al((void **)&w.rz[0], m * sizeof(float2));
+    al((void **)&w.rz[1], m * sizeof(float2));
+    al((void **)&w.list, n * sizeof(int));
+    al((void **)&w.list_tmp, sizeof(int));
+    al((void **)&w.ulog, n * sizeof(UndoEntry));
+    al((void **)&w.dlog, n * sizeof(UndoEntry));
+    al((void **)&w.bcnt, m * sizeof(int));
+    al((void **)&w.bkt, m * RL0_BUCKET * sizeof(int));
+    al((void **)&w.l1part, nchunks * sizeof(double));
+    al((void **)&w.hk_scratch, n * sizeof(unsigned long long));
+    al((void **)&w.st, sizeof(DecodeState));
+    al((void **)&w.ctx, sizeof(DecodeCtx));
+    al((void **)&w.thr, RL0_MAX_ROUNDS * sizeof(RoundThr));
+    al((void **)&w.rlog, RL0_MAX_ROUNDS * sizeof(RoundLog));
+    al((void **)&w.final_part, nchunks * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(w.bcnt, 0, m * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w.st, 0, sizeof(DecodeState));
+    if (e == cudaSuccess) e = cudaMallocHost(&A->host_pinned, sizeof(HostStage));
+    if (e != cudaSuccess) { cudaGetLastError(); return rl0_cuda_err(e); }
+    A->host_pinned_bytes = sizeof(HostStage);
+    GraphCache *gc = new (std::nothrow) GraphCache;
+    if (!gc) return RL0_ERR_ALLOC;
+    A->graph_cache = gc;
+    e = cudaStreamCreateWithFlags(&gc->capture_stream, cudaStreamNonBlocking);
+    return rl0_cuda_err(e);
+}
+
+void rl0_workspace_free(rl0_expander *A)
+{
+    Workspace &w = A->ws;
+    GraphCache *gc = (GraphCache *)A->graph_cache;
+    if (gc) {
+        for (auto &g : gc->entries) cudaGraphExecDestroy(g.exec);
+        if (gc->capture_stream) cudaStreamDestroy(gc->capture_stream);
+        delete gc;
+        A->graph_cache = nullptr;
+    }
+    void *ptrs[] = {w.rz[0], w.rz[1], w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt, w.l1part,
+                    w.hk_scratch, w.st, w.ctx, w.thr, w.rlog, w.final_part};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    std::memset(&w, 0, sizeof(w));
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
+                         float *xhat_dev, rl0_stats *stats, cudaStream_t s)
+{
+    rl0_expander *A = const_cast<rl0_expander *>(Ac);
+    Resolved R;
+    int rc = resolve(A, k, params, &R);
+    if (rc) return rc;
+    HostStage *H = (HostStage *)A->host_pinned;
+    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    H->ctx.y = y_dev;
+    H->ctx.x = xhat_dev;
+    H->ctx.want_log = 1;
+    H->ctx.passed = nullptr;
+    const Workspace &w = A->ws;
+    CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+    const int dmax = dmax_of(A->d);
+    GraphCache *gc = (GraphCache *)A->graph_cache;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : gc->entries)
+        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator) exec = g.exec;
+    if (!exec) {
+        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, &exec);
+        if (rc) return rc;
+        gc->entries.push_back(GraphEntry{R.nrounds, dmax, R.indicator, exec});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, s));
+    }
+    CK(cudaGraphLaunch(exec, s));
+    if (stats) CK(cudaEventRecord(e1, s));
+    CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    const int nchunks = (int)rl0_div_up(A->m, RL0_ROWS_CHUNK);
+    std::vector<double> part(nchunks);
+    CK(cudaMemcpyAsync(part.data(), w.final_part, nchunks * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(H->log, w.rlog, R.nrounds * sizeof(RoundLog), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        double l1 = 0.0;
+        for (double v : part) l1 += v;
+        std::memset(stats, 0, sizeof(*stats));
+        stats->rounds = H->st.rounds_run;
+        stats->accepted_rounds = H->st.accepted_rounds;
+        stats->converged = H->st.converged;
+        stats->status = H->st.status;
+        stats->support_size = H->st.shat_count;
+        stats->final_l1 = l1;
+        stats->ms = ms;
+        stats->hk_rounds = H->st.hk_rounds;
+        stats->fallback_rounds = H->st.fallback_rounds;
+    }
+    A->last_log_rounds = H->st.rounds_run;
+    return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
+}
+
+extern "C" int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap)
+{
+    if (!A || (!out && cap > 0) || cap < 0) return RL0_ERR_INVALID_ARG;
+    const HostStage *H = (const HostStage *)A->host_pinned;
+    const int nr = A->last_log_rounds < cap ? A->last_log_rounds : cap;
+    for (int r = 0; r < nr; ++r) {
+        out[r].t = H->thr[r].t;
+        out[r].l1_candidate = H->log[r].l1_candidate;
+        out[r].l1_hat = H->log[r].l1_hat;
+        out[r].accepted = H->log[r].accepted;
+        out[r].updated = H->log[r].updated;
+        out[r].support = H->log[r].support;
+        out[r].hk_dropped = H->log[r].hk_dropped;
+    }
+    return A->last_log_rounds;
+}
+
+extern "C" int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
+                          float *xhat_dev, rl0_stats *stats, void *cuda_stream)
+{
+    if (!A || !y_dev || !xhat_dev) return RL0_ERR_INVALID_ARG;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    return decode_common(A, y_dev, k, params, xhat_dev, stats, (cudaStream_t)cuda_stream);
+}
+
+extern "C" int rl0_decode_host(const rl0_expander *A, const float *y_host, int64_t k, const rl0_params *params,
+                               float *xhat_host, rl0_stats *stats, void *cuda_stream)
+{
+    if (!A || !y_host || !xhat_host) return RL0_ERR_INVALID_ARG;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float *yd = nullptr, *xd = nullptr;
+    CK(cudaMallocAsync(&yd, (size_t)A->m * 4, s));
+    cudaError_t e = cudaMallocAsync(&xd, (size_t)A->n * 4, s);
+    if (e != cudaSuccess) { cudaFreeAsync(yd, s); return rl0_cuda_err(e); }
+    e = cudaMemcpyAsync(yd, y_host, (size_t)A->m * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) rc = decode_common(A, yd, k, params, xd, stats, s);
+    else rc = rl0_cuda_err(e);
+    if (rc == RL0_OK) {
+        e = cudaMemcpyAsync(xhat_host, xd, (size_t)A->n * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = rl0_cuda_err(e);
+    }
+    cudaFreeAsync(yd, s);
+    cudaFreeAsync(xd, s);
+    return rc;
+}
+
+__global__ void k_copy_f(const float *src, float *dst, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
+                              int round_index, const float *xhat_dev, const float *rhat_dev, float *xp_dev,
+                              float *rp_dev, int32_t *passed_dev, double *l1_out, void *cuda_stream)
+{
+    rl0_expander *A = const_cast<rl0_expander *>(Ac);
+    if (!A || !y_dev || !xhat_dev || !rhat_dev || !xp_dev || !rp_dev || round_index < 0) return RL0_ERR_INVALID_ARG;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Resolved R;
+    rc = resolve(A, k, params, &R);
+    if (rc) return rc;
+    if (round_index >= RL0_MAX_ROUNDS) return RL0_ERR_INVALID_ARG;
+    R.nrounds = round_index + 1;
+    R.stop_level = -1.0;                          // never "converged" here
+    R.stop_rel = 0.0;
+    HostStage *H = (HostStage *)A->host_pinned;
+    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    H->ctx.y = y_dev;
+    H->ctx.x = xp_dev;
+    H->ctx.want_log = 0;
+    H->ctx.passed = passed_dev;
+    const Workspace &w = A->ws;
+    CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+    const KArgs a = make_args(A);
+    k_copy_f<<<2 * a.nsm, 256, 0, s>>>(xhat_dev, xp_dev, a.n);
+    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, rhat_dev, 0);
+    k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
+    k_start<<<1, 32, 0, s>>>(a, round_index, 0);
+    k_list_count_from_support<<<1, 32, 0, s>>>(a);
+    launch_round(a, dmax_of(A->d), R.indicator, s);
+    k_extract_r<<<2 * a.nsm, 256, 0, s>>>(a, rp_dev, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    const int nchunks = a.nchunks;
+    std::vector<double> part(nchunks);
+    CK(cudaMemcpyAsync(part.data(), w.l1part, nchunks * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    if (l1_out) {
+        if (H->st.upd_count > 0) {
+            double l1 = 0.0;
+            for (int c = 0; c < nchunks; ++c) l1 += part[c];
+            *l1_out = l1;
+        } else {
+            *l1_out = H->st.l1_hat;
+        }
+    }
+    return RL0_OK;
+}
+
+extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const float *const *y_dev,
+                                  const int64_t *k, const rl0_params *params, float *const *xhat_dev,
+                                  rl0_stats *stats, void *cuda_stream)
+{
+    (void)count; (void)A; (void)y_dev; (void)k; (void)params; (void)xhat_dev; (void)stats; (void)cuda_stream;
+    return RL0_ERR_UNSUPPORTED;
+}
