@@ -498,10 +498,13 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                 for (int l = 0; l < d; ++l) { lhs += fabs(rl[l] - w); rhs += fabs(rl[l]); }
             }
             double score = ne - nz;
-            double m1 = fabs(score - p->alpha);
-            double m2 = fabs(rhs - lhs) / (rhs > 0.0 ? rhs : 1.0);
-            if (m1 < margin) margin = m1;
-            if (m2 < margin) margin = m2;
+            /* distance of this anchor's pass/fail decision from flipping: the
+             * decision is (score >= alpha) and (lhs <= rhs), so its signed
+             * slack is the smaller of the two slacks */
+            double m1 = score - p->alpha;
+            double m2 = (rhs - lhs) / (rhs > 0.0 ? rhs : 1.0);
+            double slack = fabs(m1 < m2 ? m1 : m2);
+            if (slack < margin) margin = slack;
             if (lhs <= rhs && score >= p->alpha) {
                 if (best < 0 || score > best_score) { best = s; best_score = score; best_w = w; }
             }
