@@ -498,12 +498,25 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                 for (int l = 0; l < d; ++l) { lhs += fabs(rl[l] - w); rhs += fabs(rl[l]); }
             }
             double score = ne - nz;
-            /* distance of this anchor's pass/fail decision from flipping: the
-             * decision is (score >= alpha) and (lhs <= rhs), so its signed
-             * slack is the smaller of the two slacks */
+            /* Diagnostic only: how far this anchor's pass/fail decision is from
+             * flipping under rounding.  The decision is (score >= alpha) and
+             * (lhs <= rhs).  Continuous scores are soft, so the slack is the
+             * smaller of the two slacks.  Quantised counts are exact integers:
+             * only the l1 test (when the count test passes) and the q_e
+             * threshold comparisons of the pairs are rounding-sensitive.       */
             double m1 = score - p->alpha;
             double m2 = (rhs - lhs) / (rhs > 0.0 ? rhs : 1.0);
-            double slack = fabs(m1 < m2 ? m1 : m2);
+            double slack;
+            if (p->quantised) {
+                slack = (m1 >= 0.0) ? fabs(m2) : INFINITY;
+                for (int l = 0; l < d; ++l) {
+                    if (l == s) continue;
+                    double g = fabs(orc_log_pbreve(&P->pe, ri - rl[l]) - log(t));
+                    if (g < slack) slack = g;
+                }
+            } else {
+                slack = fabs(m1 < m2 ? m1 : m2);
+            }
             if (slack < margin) margin = slack;
             if (lhs <= rhs && score >= p->alpha) {
                 if (best < 0 || score > best_score) { best = s; best_score = score; best_w = w; }
