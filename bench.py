@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the Robust-l0 decoder (arXiv 1704.09012, Algorithm 2) on one GB300.
+
+A step is one whole decode (every round of the sweep t = 1, 1-c, ... > 0, or until the
+stopping level) of one synthetic instance drawn from the generating model
+GM(n, m, k, d, N(0,1), N(0, sigma_n^2)) at n = 2^20, delta = m/n = 0.1, rho = k/m = 0.1,
+d = 7, SNR 40 dB, continuous scores.  Instances are drawn once and stay in HBM; L2 is
+flushed (a 256 MiB write) between timed steps.
+
+Printed value: nnz(A) * rounds / s over all ranks (each rank decodes its own instance:
+weak scaling).  ms_per_step is the time to recover one instance.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this project has) on a
+bounded sample of the same workload: each step is one full-size round.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to recover & nnz(A)*rounds/s at n=2^20,d=7; batched/learned vs plain"
+UNIT = "nnz*rounds/s"
+L2_FLUSH_BYTES = 256 << 20
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def workload():
+    import gm
+    cfg = gm.config_large()
+    cfg["snr_db"] = 40.0
+    return cfg
+
+
+def config_dict(cfg, variant, extra=None):
+    d = {
+        "workload": "Robust-l0 %s decode, n=2^20, m=%d, k=%d, d=%d, SNR 40 dB (sigma_n=%.4g), "
+                    "Gaussian signal, 1 instance per step per GPU" % (variant, cfg["m"], cfg["k"], cfg["d"],
+                                                                   cfg["sigma_n"]),
+        "n": cfg["n"], "m": cfg["m"], "k": cfg["k"], "d": cfg["d"], "sigma_n": cfg["sigma_n"],
+        "scores": variant,
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        under_load = [v for v in sm if smax and v > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(under_load) if under_load else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the sources still match."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC)).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(cfg, seed, budget_s=20.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample: full-size rounds
+    from the start of the decode (x_hat = 0) until the time budget is spent."""
+    import numpy as np
+    import gm
+    import oracle
+    n, m, k, d, sn = cfg["n"], cfg["m"], cfg["k"], cfg["d"], cfg["sigma_n"]
+    rows = oracle.make_expander(n, m, d, seed)
+    x, _ = gm.draw_signal(n, k, 1.0, seed)
+    y = oracle.sketch(rows, x.astype(np.float64), m, sigma_n=sn, noise_seed=seed + 1)
+    y = y.astype(np.float32).astype(np.float64)
+    xh = np.zeros(n)
+    rh = y.copy()
+    rounds = 0
+    t0 = time.perf_counter()
+    while True:
+        xp, rp, upd, _ = oracle.round_step(rows, y, k, rounds + 1, xh, rh, sigma_n=sn)
+        rounds += 1
+        if np.abs(rp).sum() < np.abs(rh).sum():
+            xh, rh = xp, rp
+        if time.perf_counter() - t0 > budget_s or rounds >= 40:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * d * rounds / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d full-size rounds (t = 1-c .. 1-%dc) of the n=2^20 decode from x_hat=0, FP64, "
+                      "single thread, %.1f s" % (rounds, rounds, dt)}
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import gm
+    import oracle
+    n, m, k, d, sn = cfg["n"], cfg["m"], cfg["k"], cfg["d"], cfg["sigma_n"]
+    rows = oracle.make_expander(n, m, d, 0)
+    x, _ = gm.draw_signal(n, k, 1.0, 0)
+    y = oracle.sketch(rows, x.astype(np.float64), m, sigma_n=sn, noise_seed=1).astype(np.float32).astype(np.float64)
+    xh = np.zeros(n)
+    rh = y.copy()
+
+    def one(r):
+        nonlocal xh, rh
+        xp, rp, _, _ = oracle.round_step(rows, y, k, 1 + (r % 39), xh, rh, sigma_n=sn)
+        if np.abs(rp).sum() < np.abs(rh).sum():
+            xh, rh = xp, rp
+
+    for w in range(args.warmup):
+        one(w)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        one(args.warmup + s)
+    dt = time.perf_counter() - t0
+    value = n * d * args.steps / dt
+    sample = "each step: one full-size round of the n=2^20 decode (FP64 oracle, single thread)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_dict(cfg, "continuous", {"reference": "FP64 CPU oracle (plain C)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quantised", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    cfg = workload()
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import gm
+    import paper_1704_09012_gb300 as rl0
+    from paper_1704_09012_gb300 import build as _b
+    _b.build()
+    n, m, k, d, sn = cfg["n"], cfg["m"], cfg["k"], cfg["d"], cfg["sigma_n"]
+    nnz = n * d
+    seed = 1000 + rank
+    A = rl0.Expander.random(n, m, d, seed=seed)
+    x, _ = gm.draw_signal(n, k, 1.0, seed)
+    x_dev = torch.from_numpy(x).cuda()
+    y_dev = rl0.sketch(A, x_dev, sigma_n=sn, noise_seed=seed + 1)
+    xhat = torch.empty(n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    params = dict(sigma_n=sn, quantised=args.quantised)
+    variant = "quantised" if args.quantised else "continuous"
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        rl0.decode(A, y_dev, k, out=xhat, **params)
+    # ---- timed region: K whole decodes, device-timed, L2 flushed in between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            _, st = rl0.decode(A, y_dev, k, out=xhat, **params)
+            ev[s][1].record(stream)
+            stats.append(st)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    rounds = stats[-1]["rounds"]
+    if ws > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    units = ws * args.steps * nnz * rounds
+    value = units / t_dev
+    xr = xhat.cpu().numpy().astype(np.float64)
+    rel_l1 = float(np.abs(xr - x).sum() / np.abs(x).sum())
+
+    # ---- e2e: the same decode through the host-buffer C-ABI call (copies inside the timed region)
+    y_host = y_dev.cpu().pin_memory()
+    x_host = torch.empty(n, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        rl0.decode_host(A, y_host, k, out=x_host, **params)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for s in range(args.steps):
+        flush.zero_()
+        ev2[s][0].record(stream)
+        rl0.decode_host(A, y_host, k, out=x_host, **params)
+        ev2[s][1].record(stream)
+    barrier()
+    t_e2e = sum(a.elapsed_time(b) for a, b in ev2) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = ws * args.steps * nnz * rounds / t_e2e
+
+    # ---- per-kernel device time: event nodes captured around each kernel group
+    prof = []
+    for s in range(args.steps):
+        flush.zero_()
+        _, st = rl0.decode(A, y_dev, k, out=xhat, profile=True, **params)
+        prof.append(st)
+    launches_score = rounds * len(prof)
+    ms_score = sum(p["ms_score"] for p in prof) / launches_score
+    alg_bytes = 4 * nnz + 8 * m          # row ids (4 B per nonzero) + (r, p_z) of every row once
+    achieved = alg_bytes / (ms_score * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    group_ms = {g: sum(p["ms_" + g] for p in prof) / len(prof) for g in ("score", "hk", "rebuild", "accept")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(cfg, variant, {"rounds_per_decode": rounds, "parallelism": "replicas" if ws > 1 else "1 GPU"}),
+        "ms_to_recover": 1e3 * t_dev / args.steps,
+        "recovery": {"converged": stats[-1]["converged"], "support": stats[-1]["support_size"],
+                     "rel_l1_err": rel_l1, "accepted_rounds": stats[-1]["accepted_rounds"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": stats[-1]["launches"] * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_column_score", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic_for("k_column_score"), "alg_bytes_per_launch": alg_bytes,
+                     "avg_launch_ms": ms_score},
+        "kernel_group_ms_per_decode": group_ms,
+        "clocks": clk.summary(),
+        "wall_s": t_wall,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, seed)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

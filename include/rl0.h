@@ -63,6 +63,8 @@ typedef struct {
     double mlp_threshold;  /* scorer = 1: accept a column when its score >= this; 0 = 0.5     */
     int    max_rounds;     /* cap on the number of rounds; 0 = every round with t > 0         */
     double noiseless_tol;  /* sigma_n = 0: |a - b| <= tol counts as equal; 0 = 1e-5           */
+    int    profile;        /* 1: time each kernel group with CUDA events captured into the    */
+                           /* round graph and report it in rl0_stats.ms_* (adds event nodes)  */
 } rl0_params;
 
 /* Per-decode statistics (host structure filled by the library). */
@@ -76,6 +78,13 @@ typedef struct {
     float   ms;                /* device time of the decode (CUDA events), milliseconds      */
     int     hk_rounds;         /* rounds in which H_k had to drop entries                    */
     int     fallback_rounds;   /* rounds whose residual took the full CSR rebuild            */
+    /* profile = 1 only: summed device time of each kernel group over the rounds, and
+     * the number of kernel launches of the decode (all rounds of the replayed graph) */
+    float   ms_score;          /* column scoring                                             */
+    float   ms_hk;             /* H_k selection                                              */
+    float   ms_rebuild;        /* scatter + residual rebuild                                 */
+    float   ms_accept;         /* accept / undo                                              */
+    int     launches;          /* kernels launched by the decode                             */
 } rl0_stats;
 
 /* Def. "Generating model", item 1: draw A with each column's support uniform

@@ -45,7 +45,7 @@ class Params(C.Structure):
         ("sigma_s", C.c_double), ("sigma_n", C.c_double), ("quantised", C.c_int), ("adaptive_k", C.c_int),
         ("c", C.c_double), ("alpha", C.c_double), ("ell", C.c_int), ("scorer", C.c_int),
         ("mlp", C.c_void_p), ("mlp_threshold", C.c_double), ("max_rounds", C.c_int),
-        ("noiseless_tol", C.c_double),
+        ("noiseless_tol", C.c_double), ("profile", C.c_int),
     ]
 
 
@@ -53,7 +53,8 @@ class Stats(C.Structure):
     _fields_ = [
         ("rounds", C.c_int), ("accepted_rounds", C.c_int), ("converged", C.c_int), ("status", C.c_int),
         ("support_size", C.c_int64), ("final_l1", C.c_double), ("ms", C.c_float), ("hk_rounds", C.c_int),
-        ("fallback_rounds", C.c_int),
+        ("fallback_rounds", C.c_int), ("ms_score", C.c_float), ("ms_hk", C.c_float),
+        ("ms_rebuild", C.c_float), ("ms_accept", C.c_float), ("launches", C.c_int),
     ]
 
     def as_dict(self):
@@ -122,10 +123,10 @@ def _dev(t, dtype, n=None, what="tensor"):
 
 
 def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell=0, scorer=0, mlp=None,
-                mlp_threshold=0.0, max_rounds=0, noiseless_tol=0.0, adaptive_k=False):
+                mlp_threshold=0.0, max_rounds=0, noiseless_tol=0.0, adaptive_k=False, profile=False):
     mlp_ptr = mlp.data_ptr() if isinstance(mlp, torch.Tensor) else mlp
     return Params(sigma_s, sigma_n, int(quantised), int(adaptive_k), c, alpha, ell, scorer, mlp_ptr,
-                  mlp_threshold, max_rounds, noiseless_tol)
+                  mlp_threshold, max_rounds, noiseless_tol, int(profile))
 
 
 class Expander:

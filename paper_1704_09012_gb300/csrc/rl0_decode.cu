@@ -720,6 +720,7 @@ int resolve(const rl0_expander *A, int64_t k, const rl0_params *in, Resolved *R)
     int nr = (int)std::ceil(1.0 / p.c - 1e-9);
     if (p.max_rounds > 0 && p.max_rounds < nr) nr = p.max_rounds;
     if (nr > RL0_MAX_ROUNDS) return RL0_ERR_UNSUPPORTED;
+    if (p.profile != 0 && p.profile != 1) return RL0_ERR_INVALID_ARG;
     R->p = p;
     R->nrounds = nr;
     R->indicator = p.quantised || p.sigma_n == 0.0;
@@ -778,9 +779,13 @@ void fill_tables(const rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx 
 }
 
 struct GraphEntry {
-    int nrounds, dmax, indicator;
+    int nrounds, dmax, indicator, profile;
     cudaGraphExec_t exec;
+    std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
+
+// Kernels one decode graph launches: prologue (3), 6 per round, final check (1).
+int launches_per_decode(int nrounds) { return 3 + 6 * nrounds + 1; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -842,24 +847,46 @@ void launch_round(const KArgs &a, int dmax, int indicator, cudaStream_t s)
     k_rebuild<true><<<a.nchunks, 256, 0, s>>>(a);
 }
 
-int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, cudaGraphExec_t *out)
+int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int profile, GraphEntry *E)
 {
     GraphCache *gc = (GraphCache *)A->graph_cache;
     const KArgs a = make_args(A);
     cudaStream_t s = gc->capture_stream;
     cudaGraph_t g = nullptr;
+    E->nrounds = nrounds;
+    E->dmax = dmax;
+    E->indicator = indicator;
+    E->profile = profile;
+    if (profile) {
+        E->events.resize(4 * nrounds + 1);
+        for (auto &ev : E->events) CK(cudaEventCreate(&ev));
+    }
+    auto mark = [&](int idx) -> cudaError_t {
+        return profile ? cudaEventRecordWithFlags(E->events[idx], s, cudaEventRecordExternal) : cudaSuccess;
+    };
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
     k_rows_from<<<a.nchunks, 256, 0, s>>>(a, nullptr, 0);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
-    for (int r = 0; r < nrounds; ++r) {
-        launch_round(a, dmax, indicator, s);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < nrounds && e == cudaSuccess; ++r) {
+        e = mark(4 * r);
+        launch_column_score(a, dmax, indicator, s);
+        if (e == cudaSuccess) e = mark(4 * r + 1);
+        k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
+        if (e == cudaSuccess) e = mark(4 * r + 2);
+        k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
+        k_rebuild<false><<<a.nchunks, 256, 0, s>>>(a);
+        k_rebuild<true><<<a.nchunks, 256, 0, s>>>(a);
+        if (e == cudaSuccess) e = mark(4 * r + 3);
         k_accept<<<1, 1024, 0, s>>>(a);
     }
+    if (e == cudaSuccess) e = mark(4 * nrounds);
     k_final_l1<<<a.nchunks, 256, 0, s>>>(a);
-    cudaError_t e = cudaStreamEndCapture(s, &g);
-    if (e != cudaSuccess) return rl0_cuda_err(e);
-    e = cudaGraphInstantiate(out, g, 0);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return rl0_cuda_err(e); }
+    if (e2 != cudaSuccess) return rl0_cuda_err(e2);
+    e = cudaGraphInstantiate(&E->exec, g, 0);
     cudaGraphDestroy(g);
     return rl0_cuda_err(e);
 }
@@ -917,7 +944,10 @@ void rl0_workspace_free(rl0_expander *A)
     Workspace &w = A->ws;
     GraphCache *gc = (GraphCache *)A->graph_cache;
     if (gc) {
-        for (auto &g : gc->entries) cudaGraphExecDestroy(g.exec);
+        for (auto &g : gc->entries) {
+            cudaGraphExecDestroy(g.exec);
+            for (auto ev : g.events) cudaEventDestroy(ev);
+        }
         if (gc->capture_stream) cudaStreamDestroy(gc->capture_stream);
         delete gc;
         A->graph_cache = nullptr;
@@ -950,14 +980,21 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     const int dmax = dmax_of(A->d);
     GraphCache *gc = (GraphCache *)A->graph_cache;
-    cudaGraphExec_t exec = nullptr;
+    const int prof = R.p.profile ? 1 : 0;
+    GraphEntry *E = nullptr;
     for (auto &g : gc->entries)
-        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator) exec = g.exec;
-    if (!exec) {
-        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, &exec);
-        if (rc) return rc;
-        gc->entries.push_back(GraphEntry{R.nrounds, dmax, R.indicator, exec});
+        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator && g.profile == prof) E = &g;
+    if (!E) {
+        GraphEntry fresh;
+        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, prof, &fresh);
+        if (rc) {
+            for (auto ev : fresh.events) if (ev) cudaEventDestroy(ev);
+            return rc;
+        }
+        gc->entries.push_back(fresh);
+        E = &gc->entries.back();
     }
+    cudaGraphExec_t exec = E->exec;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (stats) {
         CK(cudaEventCreate(&e0));
@@ -990,6 +1027,20 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         stats->ms = ms;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
+        stats->launches = launches_per_decode(R.nrounds);
+        if (prof) {
+            float acc[4] = {0, 0, 0, 0};
+            for (int r = 0; r < R.nrounds; ++r)
+                for (int q = 0; q < 4; ++q) {
+                    float v = 0.0f;
+                    if (cudaEventElapsedTime(&v, E->events[4 * r + q], E->events[4 * r + q + 1]) == cudaSuccess)
+                        acc[q] += v;
+                }
+            stats->ms_score = acc[0];
+            stats->ms_hk = acc[1];
+            stats->ms_rebuild = acc[2];
+            stats->ms_accept = acc[3];
+        }
     }
     A->last_log_rounds = H->st.rounds_run;
     return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;

@@ -138,7 +138,7 @@ def _compare_round(rl0, A, I, y32, rows, k, ridx, x32, r32, quantised):
         scale = np.abs(y64) + Aabs @ np.abs(xo)
         assert np.all(np.abs(rg - ro) <= 4 * scale * 2 ** -24 + Aabs @ np.abs(xg - xo) + 1e-30)
         assert l1g == pytest.approx(np.abs(ro).sum(), rel=1e-6)
-    return int(near.sum()), int(po.sum())
+    return int(near.sum()), int(po.sum()), int(near.size)
 
 
 @pytest.mark.parametrize("quantised", [False, True])
@@ -150,14 +150,16 @@ def test_round_step_matches_oracle(rl0, quantised, cfg):
     A = rl0.Expander.from_rows(_cuda(I.rows), I.m)
     rng = np.random.default_rng(0)
     c = oracle.default_c(quantised, I.m / I.n, I.k / I.m)
-    total_near = total_pass = 0
+    total_near = total_pass = total_cols = 0
     for x32, r32 in _states(I, y32.astype(np.float64), rng):
         for ridx in (1, int(0.3 / c), int(0.8 / c)):
-            nr, np_ = _compare_round(rl0, A, I, y32, I.rows, I.k, ridx, x32, r32, quantised)
+            nr, np_, nc = _compare_round(rl0, A, I, y32, I.rows, I.k, ridx, x32, r32, quantised)
             total_near += nr
             total_pass += np_
+            total_cols += nc
     assert total_pass > 20
-    assert total_near <= max(2, total_pass // 100)
+    # rounding-sensitive decisions (excluded from the exact comparison) must be rare
+    assert total_near <= 2 + total_cols // 1000
 
 
 def test_round_step_hk_drops_with_ties(rl0):
@@ -270,8 +272,8 @@ def test_full_size_round_and_decode_properties(rl0):
     r32 = (y64 - _A(I.rows, I.m) @ x32.astype(np.float64)).astype(np.float32)
     for q in (False, True):
         c = oracle.default_c(q, I.m / I.n, I.k / I.m)
-        nr, npass = _compare_round(rl0, A, I, y32, I.rows, I.k, int(0.5 / c), x32, r32, q)
-        assert npass > 1000 and nr <= npass // 100
+        nr, npass, ncols = _compare_round(rl0, A, I, y32, I.rows, I.k, int(0.5 / c), x32, r32, q)
+        assert npass > 1000 and nr <= 2 + ncols // 1000
     # the whole decode in the benchmark's configuration: invariants at full size
     xg, st = rl0.decode(A, _cuda(y32), I.k, sigma_n=I.sigma_n)
     xg = xg.cpu().numpy().astype(np.float64)
