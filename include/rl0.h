@@ -41,6 +41,7 @@ extern "C" {
 #define RL0_ERR_UNSUPPORTED   -5   /* valid request this build does not implement    */
 #define RL0_ERR_INVALID_A     -6   /* rows out of range, duplicated or unsorted       */
 #define RL0_ERR_INVALID_Y     -7   /* y_hat holds NaN or Inf                          */
+#define RL0_ERR_TOO_LARGE     -8   /* instance exceeds rl0_decode_static's fixed workspace */
 
 /* Opaque handle: device copy of A as column-major row lists (column j owns
  * rows[j*d .. j*d+d-1], ascending), its transpose in CSR form, and the decode
@@ -153,6 +154,32 @@ int rl0_round_step(const rl0_expander *A, const float *y_dev, int64_t k, const r
 int rl0_decode_batched(int count, const rl0_expander *const *A, const float *const *y_dev,
                        const int64_t *k, const rl0_params *params, float *const *xhat_dev,
                        rl0_stats *stats, void *cuda_stream);
+
+/* rl0_decode for callers that cannot allocate memory.  (The paper has no
+ * counterpart: this is a deployment variant of Algorithm 2's loop.)
+ *
+ * Who needs it: code that must not call cudaMalloc or any other allocator
+ * while it runs -- e.g. work issued while a stream is being captured into a
+ * CUDA graph (an allocation there can synchronise the device and break the
+ * capture), real-time loops whose memory budget is fixed at start-up, or
+ * hosts whose own allocator already owns all free device memory.
+ * rl0_decode does not allocate per call either, but its first call for a
+ * given round count builds and instantiates a graph, which allocates.
+ *
+ * This entry point allocates nothing: its scratch is one file-scope device
+ * array of about 3.6 MB compiled into the library, held by every GPU that
+ * loads the library until the process exits.  The caller passes y_dev and
+ * xhat_dev as for rl0_decode and gets the same result; the kernels are
+ * launched directly on the stream.  Limits: n <= 65536, m <= 32768 (larger
+ * instances return RL0_ERR_TOO_LARGE); stats.ms and the profile fields stay 0.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array and clears the
+ * parts that must start at zero; calls that overlap on the GPU (from other
+ * streams or host threads) race on it, so serialise them. */
+int rl0_decode_static(const rl0_expander *A, const float *y_dev, int64_t k,
+                      const rl0_params *params, float *xhat_dev, rl0_stats *stats,
+                      void *cuda_stream);
 
 /* Per-round record of the last rl0_decode on this expander (host copy kept by
  * the library).  Writes min(cap, rounds) records and returns the number of

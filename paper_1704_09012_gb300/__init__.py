@@ -23,14 +23,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "librl0.so")
 RL0_OK = 0
 ERRORS = {
     -1: "RL0_ERR_INVALID_ARG", -2: "RL0_ERR_CUDA", -3: "RL0_ERR_ALLOC", -4: "RL0_ERR_TIMEOUT",
-    -5: "RL0_ERR_UNSUPPORTED", -6: "RL0_ERR_INVALID_A", -7: "RL0_ERR_INVALID_Y",
+    -5: "RL0_ERR_UNSUPPORTED", -6: "RL0_ERR_INVALID_A", -7: "RL0_ERR_INVALID_Y", -8: "RL0_ERR_TOO_LARGE",
 }
 
 # Every symbol include/rl0.h declares.
 EXPORTS = [
     "rl0_make_expander", "rl0_expander_from_rows", "rl0_expander_rows", "rl0_expander_shape",
     "rl0_free_expander", "rl0_sketch", "rl0_decode", "rl0_decode_host", "rl0_round_step",
-    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror",
+    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static",
 ]
 
 
@@ -93,6 +93,7 @@ def _lib():
         L.rl0_decode_batched.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64), vp,
                                          C.POINTER(vp), vp, vp]
         L.rl0_decode_log.argtypes = [vp, C.POINTER(RoundRecord), i32]
+        L.rl0_decode_static.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.POINTER(Stats), vp]
         L.rl0_strerror.argtypes = [i32]
         L.rl0_strerror.restype = C.c_char_p
         _L = L
@@ -189,6 +190,20 @@ def decode(A, y, k, out=None, stream=None, **params):
     st = Stats()
     _check(_lib().rl0_decode(A.handle, _dev(y, torch.float32, A.m, "y"), int(k), C.byref(p),
                              _dev(x, torch.float32, A.n, "x_hat"), C.byref(st), _stream(stream)), "rl0_decode")
+    return x, st.as_dict()
+
+
+def decode_static(A, y, k, out=None, stream=None, **params):
+    """rl0_decode without any allocation (fixed workspace inside the library; n <= 65536,
+    m <= 32768).  For callers that cannot allocate device memory while they run, e.g.
+    during stream capture or under a memory budget fixed at start-up; `out` lets them
+    pass a preallocated x_hat as well.  Calls share the workspace: do not overlap them."""
+    p = make_params(**params)
+    x = out if out is not None else torch.empty(A.n, dtype=torch.float32, device="cuda")
+    st = Stats()
+    _check(_lib().rl0_decode_static(A.handle, _dev(y, torch.float32, A.m, "y"), int(k), C.byref(p),
+                                    _dev(x, torch.float32, A.n, "x_hat"), C.byref(st), _stream(stream)),
+           "rl0_decode_static")
     return x, st.as_dict()
 
 

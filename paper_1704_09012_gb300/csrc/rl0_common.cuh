@@ -127,6 +127,10 @@ struct rl0_expander {
 
 #define RL0_MAX_ROUNDS 1024
 
+// Size limits of rl0_decode_static (its workspace is a fixed array).
+#define RL0_STATIC_MAX_N 65536
+#define RL0_STATIC_MAX_M 32768
+
 // ---- helpers shared by translation units -------------------------------
 int rl0_set_device_of(const rl0_expander *A);
 int rl0_cuda_err(cudaError_t e);

@@ -1161,3 +1161,151 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
     (void)count; (void)A; (void)y_dev; (void)k; (void)params; (void)xhat_dev; (void)stats; (void)cuda_stream;
     return RL0_ERR_UNSUPPORTED;
 }
+
+// ---------------------------------------------------------------------------
+// rl0_decode_static: the same decode with no allocation at all.
+//
+// Its working memory is one fixed array compiled into this library (below), so
+// a call never asks the CUDA allocator (or any other allocator) for memory and
+// never builds a graph (instantiating one allocates).  The price: instances are
+// limited to n <= RL0_STATIC_MAX_N and m <= RL0_STATIC_MAX_M, every GPU that
+// loads the library keeps the array (about 3.6 MB) until the process exits,
+// and all calls share it, so calls that overlap on the GPU (other streams,
+// other host threads) race and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define RL0_STATIC_CHUNKS ((RL0_STATIC_MAX_M + RL0_ROWS_CHUNK - 1) / RL0_ROWS_CHUNK)
+#define RL0_STATIC_ALIGN(x) (((x) + 255) & ~(size_t)255)
+
+// Byte layout of the static workspace (each piece 256-byte aligned).
+struct StaticLayout {
+    size_t rz0, rz1, list, ulog, dlog, bcnt, bkt, l1part, final_part, hkkey, st, ctx, thr, rlog, total;
+};
+
+static constexpr StaticLayout static_layout()
+{
+    StaticLayout L{};
+    size_t o = 0;
+    L.rz0 = o; o += RL0_STATIC_ALIGN(sizeof(float2) * RL0_STATIC_MAX_M);
+    L.rz1 = o; o += RL0_STATIC_ALIGN(sizeof(float2) * RL0_STATIC_MAX_M);
+    L.list = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_N);
+    L.ulog = o; o += RL0_STATIC_ALIGN(sizeof(UndoEntry) * RL0_STATIC_MAX_N);
+    L.dlog = o; o += RL0_STATIC_ALIGN(sizeof(UndoEntry) * RL0_STATIC_MAX_N);
+    L.bcnt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M);
+    L.bkt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M * RL0_BUCKET);
+    L.l1part = o; o += RL0_STATIC_ALIGN(sizeof(double) * RL0_STATIC_CHUNKS);
+    L.final_part = o; o += RL0_STATIC_ALIGN(sizeof(double) * RL0_STATIC_CHUNKS);
+    L.hkkey = o; o += RL0_STATIC_ALIGN(sizeof(unsigned long long) * RL0_STATIC_MAX_N);
+    L.st = o; o += RL0_STATIC_ALIGN(sizeof(DecodeState));
+    L.ctx = o; o += RL0_STATIC_ALIGN(sizeof(DecodeCtx));
+    L.thr = o; o += RL0_STATIC_ALIGN(sizeof(RoundThr) * RL0_MAX_ROUNDS);
+    L.rlog = o; o += RL0_STATIC_ALIGN(sizeof(RoundLog) * RL0_MAX_ROUNDS);
+    L.total = o;
+    return L;
+}
+
+static constexpr StaticLayout kStaticLayout = static_layout();
+
+// The scratch array itself.  In host code this name is only a stand-in for
+// the device object; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_rl0_static_scratch[kStaticLayout.total];
+
+#define RL0_STATIC_MAX_DEVICES 64
+static std::mutex g_static_mutex;
+static void *g_static_base[RL0_STATIC_MAX_DEVICES];
+
+// Device address of the scratch array on device `dev` (which must be current);
+// looked up once per device, on the first call that runs there.
+static int static_scratch_base(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= RL0_STATIC_MAX_DEVICES) return RL0_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rl0_static_scratch);
+        if (e != cudaSuccess || !p) return rl0_cuda_err(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_static_base[dev] = p;
+    }
+    *out = (unsigned char *)g_static_base[dev];
+    return RL0_OK;
+}
+
+extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
+                                 float *xhat_dev, rl0_stats *stats, void *cuda_stream)
+{
+    rl0_expander *A = const_cast<rl0_expander *>(Ac);
+    if (!A || !y_dev || !xhat_dev) return RL0_ERR_INVALID_ARG;
+    if (A->n > RL0_STATIC_MAX_N || A->m > RL0_STATIC_MAX_M) return RL0_ERR_TOO_LARGE;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    Resolved R;
+    rc = resolve(A, k, params, &R);
+    if (rc) return rc;
+    unsigned char *base = nullptr;
+    rc = static_scratch_base(A->device, &base);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const StaticLayout &L = kStaticLayout;
+
+    KArgs a = make_args(A);
+    a.rz0 = (float2 *)(base + L.rz0);
+    a.rz1 = (float2 *)(base + L.rz1);
+    a.list = (int *)(base + L.list);
+    a.ulog = (UndoEntry *)(base + L.ulog);
+    a.dlog = (UndoEntry *)(base + L.dlog);
+    a.bcnt = (int *)(base + L.bcnt);
+    a.bkt = (int *)(base + L.bkt);
+    a.l1part = (double *)(base + L.l1part);
+    a.final_part = (double *)(base + L.final_part);
+    a.hkkey = (unsigned long long *)(base + L.hkkey);
+    a.st = (DecodeState *)(base + L.st);
+    a.ctx = (DecodeCtx *)(base + L.ctx);
+    a.thr = (const RoundThr *)(base + L.thr);
+    a.rlog = (RoundLog *)(base + L.rlog);
+
+    // Per-call tables go through the expander's pinned staging block, which was
+    // set up when the expander was created.
+    HostStage *H = (HostStage *)A->host_pinned;
+    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    H->ctx.y = y_dev;
+    H->ctx.x = xhat_dev;
+    H->ctx.want_log = 0;
+    H->ctx.passed = nullptr;
+    CK(cudaMemcpyAsync(base + L.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + L.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    // the array keeps the last call's contents: clear what must start at zero
+    CK(cudaMemsetAsync(base + L.st, 0, sizeof(DecodeState), s));
+    CK(cudaMemsetAsync(base + L.bcnt, 0, sizeof(int) * (size_t)A->m, s));
+
+    const int dmax = dmax_of(A->d);
+    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
+    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, nullptr, 0);
+    k_start<<<1, 32, 0, s>>>(a, 0, 1);
+    for (int r = 0; r < R.nrounds; ++r) {
+        launch_round(a, dmax, R.indicator, s);
+        k_accept<<<1, 1024, 0, s>>>(a);
+    }
+    k_final_l1<<<a.nchunks, 256, 0, s>>>(a);
+    CK(cudaGetLastError());
+    double part[RL0_STATIC_CHUNKS];
+    CK(cudaMemcpyAsync(&H->st, base + L.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(part, base + L.final_part, sizeof(double) * a.nchunks, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    if (stats) {
+        double l1 = 0.0;
+        for (int c = 0; c < a.nchunks; ++c) l1 += part[c];
+        std::memset(stats, 0, sizeof(*stats));
+        stats->rounds = H->st.rounds_run;
+        stats->accepted_rounds = H->st.accepted_rounds;
+        stats->converged = H->st.converged;
+        stats->status = H->st.status;
+        stats->support_size = H->st.shat_count;
+        stats->final_l1 = l1;
+        stats->hk_rounds = H->st.hk_rounds;
+        stats->fallback_rounds = H->st.fallback_rounds;
+        stats->launches = launches_per_decode(R.nrounds);
+    }
+    return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
+}

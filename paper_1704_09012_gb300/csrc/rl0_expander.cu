@@ -387,6 +387,7 @@ extern "C" const char *rl0_strerror(int code)
     case RL0_ERR_UNSUPPORTED: return "unsupported request";
     case RL0_ERR_INVALID_A: return "invalid expander rows (range, order or duplicates)";
     case RL0_ERR_INVALID_Y: return "y_hat holds NaN or Inf";
+    case RL0_ERR_TOO_LARGE: return "instance larger than the static workspace (n <= 65536, m <= 32768)";
     default: return "unknown error";
     }
 }
