@@ -9,7 +9,7 @@
 
 #define RL0_MAXQ 12          // explicit series terms + tail (ell <= 10)
 #define RL0_BUCKET 8         // contributors per row held by the sparse rebuild
-#define RL0_ROWS_CHUNK 1024  // rows per l1 partial (fixed: defines the summation order)
+#define RL0_ROWS_CHUNK 256   // rows per l1 partial, one row per thread (fixed: defines the summation order)
 #define RL0_MAX_D 32
 
 // Status codes a kernel can leave in DecodeState::status.
@@ -19,11 +19,22 @@
 // 1/p_breve(w) = sum_q a[q] exp(b[q] w^2), q = 0..nq-1 (Eq. (pz_approx) or
 // (pe_approx) divided through by the noise density, Eq. (breve) normalisation);
 // beyond |w| > cut the posterior is below 2^-40 and is taken as 0.
+// When use_poly is set, the q >= 1 terms are evaluated in factored form:
+//   sum_{q>=1} a_q exp(b_q u) = exp(b1 u) G(u),  u = w^2,
+// with G(u) = sum_{q>=1} a_q exp((b_q - b1) u) a slowly varying function on
+// [0, cut^2] held as a Chebyshev series (t = u * inv_u2 - 1), so one exp per
+// evaluation replaces one per term.
+#define RL0_MAXPOLY 16
 struct Series {
     int nq;
     float a[RL0_MAXQ];
     float b[RL0_MAXQ];
     float cut;
+    int use_poly;
+    int npoly;
+    float b1;
+    float inv_u2;
+    float poly[RL0_MAXPOLY];
 };
 
 // Per-round thresholds on magnitudes, FP64-derived and rounded outward so that
@@ -56,12 +67,17 @@ struct DecodeState {
     unsigned drop_count;      // entries H_k zeroed this round (undo log length)
     int overflow;             // a row had more than RL0_BUCKET contributors
     int converged;            // ||r_hat||_1 <= stop level
+    unsigned nnz;             // |supp x_hat|
+    int nnz_delta;            // change of the nonzero count made by this round's updates
+    unsigned zeroed;          // updates that made an entry exactly zero this round
+    unsigned iters;           // accept invocations (bounds the graph's while loop)
     int rounds_run;
     int accepted_rounds;
     int hk_rounds;
     int fallback_rounds;
     double l1_hat;
     double l1_new;
+    double final_l1;          // ||y_hat - A x_hat||_1 in FP64 (epilogue)
 };
 
 // Per-call data the round kernels read from device memory.  The graph that
@@ -123,6 +139,8 @@ struct rl0_expander {
     size_t host_pinned_bytes;
     int *dev_flag;            // validation flag
     int last_log_rounds;      // rounds recorded by the last rl0_decode
+    void *events;             // CUDA events used to time decodes
+    void *table_cache;        // host tables of the last parameter set
 };
 
 #define RL0_MAX_ROUNDS 1024

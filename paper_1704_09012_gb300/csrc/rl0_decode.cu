@@ -48,6 +48,8 @@ struct KArgs {
     const RoundThr *thr;
     RoundLog *rlog;
     double *final_part;
+    cudaGraphConditionalHandle cond;   // while-loop condition of the round graph
+    int has_cond;
 };
 
 // ---------------------------------------------------------------------------
@@ -57,9 +59,23 @@ __device__ __forceinline__ float series_eval(const Series &S, float w)
 {
     if (w == 0.0f) return 1.0f;                 // p_breve(0) = 1 exactly
     if (fabsf(w) > S.cut) return 0.0f;          // below 2^-40
-    const float w2 = w * w;
-    float acc = S.a[0];
-    for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * w2);
+    const float u = w * w;
+    float acc;
+    if (S.use_poly) {
+        const float t = fmaf(u, S.inv_u2, -1.0f);
+        const float t2 = 2.0f * t;
+        float b1 = 0.0f, b2 = 0.0f;
+        for (int k = S.npoly - 1; k >= 1; --k) {   // Clenshaw recurrence
+            const float b0 = fmaf(t2, b1, S.poly[k] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+        const float G = fmaf(t, b1, S.poly[0] - b2);
+        acc = fmaf(expf(S.b1 * u), G, S.a[0]);
+    } else {
+        acc = S.a[0];
+        for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * u);
+    }
     return 1.0f / acc;
 }
 
@@ -78,29 +94,23 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
     return r;
 }
 
-// r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each 1024-row chunk.
-// 256 threads per chunk, thread t handles rows t, t+256, t+512, t+768.
-__global__ void __launch_bounds__(256) k_rows_from(KArgs a, const float *src_override, int dst)
+// r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
+// chunk (one row per thread, blockDim = RL0_ROWS_CHUNK).
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const float *src_override, int dst)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[RL0_ROWS_CHUNK];
     const DecodeCtx *ctx = a.ctx;
     const float *src = src_override ? src_override : ctx->y;
     float2 *rz = dst ? a.rz1 : a.rz0;
-    const bool smooth = !ctx->indicator;
     double l1 = 0.0;
-    bool bad = false;
-    const int base = blockIdx.x * RL0_ROWS_CHUNK;
-    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
-        const int i = base + u * 256 + threadIdx.x;
-        if (i < a.m) {
-            const float r = src[i];
-            bad |= !isfinite(r);
-            const float z = smooth ? series_eval(ctx->pz, r) : 0.0f;
-            rz[i] = make_float2(r, z);
-            l1 += fabs((double)r);
-        }
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    if (i < a.m) {
+        const float r = src[i];
+        if (!isfinite(r)) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
+        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
+        rz[i] = make_float2(r, z);
+        l1 = fabs((double)r);
     }
-    if (bad) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
     const double s = block_sum_f64(l1, sh);
     if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
 }
@@ -137,6 +147,11 @@ __global__ void k_start(KArgs a, int round0, int empty_support)
     a.ctx->stop_level = stop;
     st->converged = (l1 <= stop);
     st->done = (status != 0) || st->converged || (round0 >= a.ctx->nrounds);
+    st->nnz = st->shat_count;
+    st->nnz_delta = 0;
+    st->zeroed = 0;
+    st->iters = 0;
+    if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
 }
 
 // Support list of an injected x_hat (order irrelevant: every consumer sorts
@@ -162,11 +177,32 @@ __global__ void k_list_count_from_support(KArgs a)
 
 // ---------------------------------------------------------------------------
 // Column score: Algorithm 2's loop over j in [n] and i in N(j).
+//
+// One thread per column.  Fast path (registers only): the anchors
+// (|r_i| >= ta) and, for every anchor, the mask of rows within reach of it --
+// |r_i - r_l| <= te for the 0/1 scores, or <= the 2^-40 cut of p_e for the
+// continuous scores, where n_e <= 1 + popc(mask).  An anchor whose bound
+// cannot reach n_e - n_z >= alpha is dropped here; for the 0/1 scores the
+// bound is n_e itself.  Slow path (rare): the surviving anchors, in slot
+// order, get the exact n_e, omega and l1 test from residuals kept in shared
+// memory, in the same order of operations for every launch shape.
 // ---------------------------------------------------------------------------
+// Threads per CTA of the column kernel: the shared candidate arrays scale
+// with DMAX x threads and must stay within the 48 KB of static shared memory.
+template <int DMAX> struct ColBlock { static constexpr int value = DMAX <= 8 ? 256 : (DMAX <= 16 ? 128 : 64); };
+
 template <int DMAX, bool IND>
-__global__ void __launch_bounds__(256) k_column_score(KArgs a)
+__global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
 {
+    constexpr int NT = ColBlock<DMAX>::value;
     __shared__ Series s_pe;
+    __shared__ float s_r[DMAX][NT];           // residuals of columns with candidates
+    __shared__ float s_score[DMAX][NT];       // n_e - n_z of passing candidates
+    __shared__ float s_w[DMAX][NT];           // omega of passing candidates
+    __shared__ float s_nz[NT], s_rhs[NT];
+    __shared__ unsigned s_pass[NT];           // passing anchors of each column (bit per slot)
+    __shared__ unsigned short s_q[NT * DMAX]; // candidate queue: (column lane << 5) | slot
+    __shared__ int s_nq;
     const DecodeState *st = a.st;
     if (st->done) return;
     const DecodeCtx *ctx = a.ctx;
@@ -174,77 +210,101 @@ __global__ void __launch_bounds__(256) k_column_score(KArgs a)
     const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
     const RoundThr th = a.thr[round];
     const float alpha = ctx->alpha;
-    if (!IND) {
-        if (threadIdx.x == 0) s_pe = ctx->pe;
-        __syncthreads();
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_nq = 0;
+        if (!IND) s_pe = ctx->pe;
     }
+    s_pass[tid] = 0u;
+    __syncthreads();
     const int n = a.n, d = a.d;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + tid;
     const bool active = j < n;
 
-    float r[DMAX], z[DMAX];
+    float r[DMAX];
+    float nz = 0.0f, rhs = 0.0f;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
         r[s] = 0.0f;
-        z[s] = 0.0f;
         if (s < d && active) {
             const int row = __ldg(a.rows_sm + (size_t)s * n + j);
             const float2 v = __ldg(rz + row);
             r[s] = v.x;
-            z[s] = v.y;
+            nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
+            rhs += fabsf(v.x);
         }
     }
-    float nz = 0.0f, rhs = 0.0f;
+    const float reach = IND ? th.te : s_pe.cut;
+    unsigned cand = 0;
+    if (active) {
+        unsigned amask = 0;
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-        if (s < d) {
-            nz += IND ? (fabsf(r[s]) <= th.tz ? 1.0f : 0.0f) : z[s];
-            rhs += fabsf(r[s]);
+        for (int s = 0; s < DMAX; ++s)
+            if (s < d && fabsf(r[s]) >= th.ta) amask |= 1u << s;
+        if (amask) {
+            unsigned nm[DMAX];
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) nm[s] = 0u;
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) {
+#pragma unroll
+                for (int l = s + 1; l < DMAX; ++l) {
+                    if (l < d && fabsf(r[s] - r[l]) <= reach) {
+                        nm[s] |= 1u << l;
+                        nm[l] |= 1u << s;
+                    }
+                }
+            }
+            const float need = IND ? alpha : alpha - 1e-3f;
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (((amask >> s) & 1u) && (1.0f + (float)__popc(nm[s])) - nz >= need) cand |= 1u << s;
         }
     }
+    if (cand) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
+        s_nz[tid] = nz;
+        s_rhs[tid] = rhs;
+        int base = atomicAdd(&s_nq, __popc(cand));
+        for (unsigned c = cand; c; c &= c - 1u) s_q[base++] = (unsigned short)((tid << 5) | (__ffs(c) - 1));
+    }
+    __syncthreads();
+    // exact scores of the queued (column, anchor) pairs, spread over the whole CTA
+    const int nq = s_nq;
+    for (int e = tid; e < nq; e += NT) {
+        const int owner = s_q[e] >> 5, s = s_q[e] & 31;
+        const float rs = s_r[s][owner];
+        float ne = 0.0f, num = 0.0f;
+#pragma unroll 1
+        for (int l = 0; l < d; ++l) {
+            const float rl = s_r[l][owner];
+            const float q = IND ? (fabsf(rs - rl) <= th.te ? 1.0f : 0.0f) : series_eval(s_pe, rs - rl);
+            ne += q;
+            num += rl * q;
+        }
+        const float w = num / ne;
+        float lhs = 0.0f;
+#pragma unroll 1
+        for (int l = 0; l < d; ++l) lhs += fabsf(s_r[l][owner] - w);
+        const float score = ne - s_nz[owner];
+        if (lhs <= s_rhs[owner] && score >= alpha) {
+            s_score[s][owner] = score;
+            s_w[s][owner] = w;
+            atomicOr(&s_pass[owner], 1u << s);
+        }
+    }
+    __syncthreads();
+    // the best passing anchor of the column: largest n_e - n_z, ties to the lowest slot
     int best = -1;
     float bscore = 0.0f, bw = 0.0f;
-    if (active) {
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            if (s >= d || !(fabsf(r[s]) >= th.ta)) continue;     // anchor: 1 - p_z(r_i) >= t
-            float ne = 0.0f, num = 0.0f;
-            if (IND) {
-#pragma unroll
-                for (int l = 0; l < DMAX; ++l) {
-                    if (l < d) {
-                        const float q = (fabsf(r[s] - r[l]) <= th.te) ? 1.0f : 0.0f;
-                        ne += q;
-                        num += r[l] * q;
-                    }
-                }
-            } else {
-                // n_e <= 1 + #{l != i : |r_i - r_l| <= cut}: skip anchors that cannot pass
-                int near = 0;
-#pragma unroll
-                for (int l = 0; l < DMAX; ++l)
-                    if (l < d && l != s && fabsf(r[s] - r[l]) <= s_pe.cut) ++near;
-                if ((1.0f + (float)near) - nz < alpha - 1e-3f) continue;
-#pragma unroll
-                for (int l = 0; l < DMAX; ++l) {
-                    if (l < d) {
-                        const float q = series_eval(s_pe, r[s] - r[l]);
-                        ne += q;
-                        num += r[l] * q;
-                    }
-                }
-            }
-            const float w = num / ne;
-            float lhs = 0.0f;
-#pragma unroll
-            for (int l = 0; l < DMAX; ++l)
-                if (l < d) lhs += fabsf(r[l] - w);
-            const float score = ne - nz;
-            if (lhs <= rhs && score >= alpha && (best < 0 || score > bscore)) {
-                best = s;
-                bscore = score;
-                bw = w;
-            }
+    for (unsigned pm = s_pass[tid]; pm; pm &= pm - 1u) {
+        const int s = __ffs(pm) - 1;
+        const float sc = s_score[s][tid];
+        if (best < 0 || sc > bscore) {
+            best = s;
+            bscore = sc;
+            bw = s_w[s][tid];
         }
     }
     const bool pass = best >= 0;
@@ -260,8 +320,14 @@ __global__ void __launch_bounds__(256) k_column_score(KArgs a)
     unsigned mask = __ballot_sync(0xffffffffu, pass);
     if (mask) {
         const int leader = __ffs(mask) - 1;
+        const int dn = __reduce_add_sync(0xffffffffu, pass ? (int)(nv != 0.0f) - (int)(old != 0.0f) : 0);
+        const unsigned gone = __popc(__ballot_sync(0xffffffffu, pass && old != 0.0f && nv == 0.0f));
         unsigned base = 0;
-        if (lane == leader) base = atomicAdd(&a.st->upd_count, (unsigned)__popc(mask));
+        if (lane == leader) {
+            if (dn) atomicAdd(&a.st->nnz_delta, dn);
+            if (gone) atomicAdd(&a.st->zeroed, gone);
+            base = atomicAdd(&a.st->upd_count, (unsigned)__popc(mask));
+        }
         base = __shfl_sync(0xffffffffu, base, leader);
         if (pass) {
             UndoEntry e;
@@ -297,7 +363,6 @@ __global__ void __launch_bounds__(HK_THREADS) k_hk_select(KArgs a)
 {
     __shared__ unsigned hist[HK_BINS];
     __shared__ unsigned suf[HK_THREADS];
-    __shared__ unsigned s_red[32];
     __shared__ unsigned long long s_prefix;
     __shared__ unsigned s_need;
     DecodeState *st = a.st;
@@ -307,27 +372,15 @@ __global__ void __launch_bounds__(HK_THREADS) k_hk_select(KArgs a)
     const unsigned total = st->list_count;
     const int t = threadIdx.x;
 
-    // keys of the nonzero entries; count them
-    unsigned cnt = 0;
+    // |supp x'| is known from the counters: nothing to do when it is at most k
+    const long long nnz = (long long)st->nnz + st->nnz_delta;
+    if (nnz <= k) return;
     for (unsigned e = t; e < total; e += HK_THREADS) {
         const int j = a.list[e];
         const float v = x[j];
-        const unsigned long long key = (v != 0.0f) ? hk_key(v, j) : 0ull;
-        a.hkkey[e] = key;
-        cnt += (v != 0.0f);
-    }
-    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
-    if ((t & 31) == 0) s_red[t >> 5] = cnt;
-    __syncthreads();
-    if (t < 32) {
-        unsigned v = s_red[t];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (t == 0) s_red[0] = v;
+        a.hkkey[e] = (v != 0.0f) ? hk_key(v, j) : 0ull;
     }
     __syncthreads();
-    const unsigned nnz = s_red[0];
-    if ((long long)nnz <= k) return;
-
     if (t == 0) { s_prefix = 0ull; s_need = (unsigned)k; }
     __syncthreads();
     const int shifts[6] = {52, 41, 30, 19, 8, 0};
@@ -408,48 +461,47 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a)
     }
 }
 
-template <bool CSR>
-__global__ void __launch_bounds__(256) k_rebuild(KArgs a)
+#define RL0_CSWAP(i, j) { const int lo_ = min(js[i], js[j]), hi_ = max(js[i], js[j]); js[i] = lo_; js[j] = hi_; }
+
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[RL0_ROWS_CHUNK];
     DecodeState *st = a.st;
     if (st->done || st->upd_count == 0) return;
-    if ((st->overflow != 0) != CSR) return;
+    const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
     const DecodeCtx *ctx = a.ctx;
     const float *x = ctx->x;
-    const float *y = ctx->y;
     float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
-    const bool smooth = !ctx->indicator;
     double l1 = 0.0;
-    const int base = blockIdx.x * RL0_ROWS_CHUNK;
-    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
-        const int i = base + u * 256 + threadIdx.x;
-        if (i >= a.m) continue;
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    if (i < a.m) {
         float sum = 0.0f;
-        if (CSR) {
+        if (csr) {
             for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
             a.bcnt[i] = 0;
         } else {
             const int c = a.bcnt[i];
             if (c > 0) {
+                static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
                 int js[RL0_BUCKET];
 #pragma unroll
                 for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
+                // ascending column order (Batcher's 19-comparator network)
+                RL0_CSWAP(0, 1) RL0_CSWAP(2, 3) RL0_CSWAP(4, 5) RL0_CSWAP(6, 7)
+                RL0_CSWAP(0, 2) RL0_CSWAP(1, 3) RL0_CSWAP(4, 6) RL0_CSWAP(5, 7)
+                RL0_CSWAP(1, 2) RL0_CSWAP(5, 6) RL0_CSWAP(0, 4) RL0_CSWAP(1, 5)
+                RL0_CSWAP(2, 6) RL0_CSWAP(3, 7) RL0_CSWAP(2, 4) RL0_CSWAP(3, 5)
+                RL0_CSWAP(1, 2) RL0_CSWAP(3, 4) RL0_CSWAP(5, 6)
 #pragma unroll
-                for (int q = 1; q < RL0_BUCKET; ++q) {          // ascending column order
-                    const int v = js[q];
-                    int p = q - 1;
-                    while (p >= 0 && js[p] > v) { js[p + 1] = js[p]; --p; }
-                    js[p + 1] = v;
-                }
-                for (int q = 0; q < c; ++q) sum += x[js[q]];
+                for (int q = 0; q < RL0_BUCKET; ++q)
+                    if (q < c) sum += x[js[q]];
                 a.bcnt[i] = 0;
             }
         }
-        const float r = y[i] - sum;
-        const float z = smooth ? series_eval(ctx->pz, r) : 0.0f;
+        const float r = ctx->y[i] - sum;
+        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
         rz[i] = make_float2(r, z);
-        l1 += fabs((double)r);
+        l1 = fabs((double)r);
     }
     const double s = block_sum_f64(l1, sh);
     if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
@@ -460,51 +512,61 @@ __global__ void __launch_bounds__(256) k_rebuild(KArgs a)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_accept(KArgs a)
 {
-    __shared__ double shd[1024];
     __shared__ unsigned shu[1024];
+    __shared__ double s_l1;
     __shared__ int s_acc;
     DecodeState *st = a.st;
-    if (st->done) return;
     const int t = threadIdx.x;
+    if (st->done) {
+        // never expected inside the loop; keeps the while-condition consistent
+        if (t == 0 && a.has_cond) cudaGraphSetConditional(a.cond, 0u);
+        return;
+    }
     const unsigned upd = st->upd_count;
     const DecodeCtx *ctx = a.ctx;
     float *x = ctx->x;
-    double l1n = st->l1_hat;
+    if (t == 0) s_acc = 0;
     if (upd > 0) {
-        double v = 0.0;
-        for (int c = t; c < a.nchunks; c += 1024) v += a.l1part[c];
-        l1n = block_sum_f64(v, shd);
-        if (t == 0) s_acc = (l1n < st->l1_hat);
+        if (t < 32) {
+            // ||r||_1 of the candidate: chunk partials combined in a fixed order
+            double v = 0.0;
+            for (int c = t; c < a.nchunks; c += 32) v += a.l1part[c];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (t == 0) { s_l1 = v; s_acc = (v < st->l1_hat); }
+        }
         __syncthreads();
         if (s_acc) {
-            // stable in-place compaction of the list to the new support
-            const unsigned total = st->list_count;
-            unsigned out = 0;
-            for (unsigned base = 0; base < total; base += 1024) {
-                const unsigned e = base + t;
-                int j = -1;
-                unsigned keep = 0;
-                if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
-                shu[t] = keep;
-                __syncthreads();
-                for (int off = 1; off < 1024; off <<= 1) {
-                    const unsigned w = (t >= off) ? shu[t - off] : 0u;
+            if (st->drop_count > 0 || st->zeroed > 0) {
+                // entries became zero: stable in-place compaction of the list
+                const unsigned total = st->list_count;
+                unsigned out = 0;
+                for (unsigned base = 0; base < total; base += 1024) {
+                    const unsigned e = base + t;
+                    int j = -1;
+                    unsigned keep = 0;
+                    if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
+                    shu[t] = keep;
                     __syncthreads();
-                    shu[t] += w;
+                    for (int off = 1; off < 1024; off <<= 1) {
+                        const unsigned w = (t >= off) ? shu[t - off] : 0u;
+                        __syncthreads();
+                        shu[t] += w;
+                        __syncthreads();
+                    }
+                    const unsigned incl = shu[t];
+                    const unsigned blk = shu[1023];
+                    __syncthreads();
+                    if (keep) a.list[out + incl - 1] = j;
+                    out += blk;
                     __syncthreads();
                 }
-                const unsigned incl = shu[t];
-                const unsigned blk = shu[1023];
-                __syncthreads();
-                if (keep) a.list[out + incl - 1] = j;
-                out += blk;
-                __syncthreads();
+                if (t == 0) st->list_count = out;
             }
             if (t == 0) {
-                st->shat_count = out;
-                st->list_count = out;
+                st->shat_count = st->list_count;
+                st->nnz = (unsigned)((int)st->nnz + st->nnz_delta - (int)st->drop_count);
                 st->cur ^= 1;
-                st->l1_hat = l1n;
+                st->l1_hat = s_l1;
                 st->accepted_rounds += 1;
             }
         } else {
@@ -518,13 +580,14 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
     }
     if (t == 0) {
         const int round = st->round;
+        const double l1n = (upd > 0) ? s_l1 : st->l1_hat;
         if (ctx->want_log && round < RL0_MAX_ROUNDS) {
             RoundLog L;
             L.l1_candidate = l1n;
             L.l1_hat = st->l1_hat;
-            L.accepted = (upd > 0) ? s_acc : 0;
+            L.accepted = s_acc;
             L.updated = (int)upd;
-            L.support = (int)st->shat_count;
+            L.support = (int)st->nnz;
             L.hk_dropped = (int)st->drop_count;
             a.rlog[round] = L;
         }
@@ -533,31 +596,41 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
         st->upd_count = 0;
         st->drop_count = 0;
         st->overflow = 0;
+        st->nnz_delta = 0;
+        st->zeroed = 0;
         st->round = round + 1;
         st->rounds_run += 1;
+        st->iters += 1;
         st->l1_new = l1n;
         st->converged = (st->l1_hat <= ctx->stop_level);
-        if (st->converged || st->round >= ctx->nrounds) st->done = 1;
+        if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds) st->done = 1;
+        if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
     }
 }
 
 // ||y - A x_hat||_1 with every step in FP64 (the final residual-norm check).
-__global__ void __launch_bounds__(256) k_final_l1(KArgs a)
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_final_l1(KArgs a)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[RL0_ROWS_CHUNK];
     const float *x = a.ctx->x;
-    const float *y = a.ctx->y;
     double l1 = 0.0;
-    const int base = blockIdx.x * RL0_ROWS_CHUNK;
-    for (int u = 0; u < RL0_ROWS_CHUNK / 256; ++u) {
-        const int i = base + u * 256 + threadIdx.x;
-        if (i >= a.m) continue;
-        double acc = (double)y[i];
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    if (i < a.m) {
+        double acc = (double)a.ctx->y[i];
         for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) acc -= (double)x[a.colidx[p]];
-        l1 += fabs(acc);
+        l1 = fabs(acc);
     }
     const double s = block_sum_f64(l1, sh);
     if (threadIdx.x == 0) a.final_part[blockIdx.x] = s;
+}
+
+// Sum of the FP64 final-residual partials in chunk order (one warp).
+__global__ void k_final_sum(KArgs a)
+{
+    double v = 0.0;
+    for (int c = threadIdx.x; c < a.nchunks; c += 32) v += a.final_part[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) a.st->final_l1 = v;
 }
 
 // round_step output: the candidate residual (or r_hat when nothing changed).
@@ -630,13 +703,28 @@ double series_F(const HostSeries &H, double w)
 }
 
 // Smallest w >= 0 with F(w) >= T (F increasing in |w|); +inf for T = inf.
+// Every q >= 1 term has b_1 <= b_q <= b_max, so with A = 1 - a_0,
+//   a_0 + A exp(b_1 w^2) <= F(w) <= a_0 + A exp(b_max w^2),
+// which brackets the root; bisection then runs to adjacent doubles.
 double series_inverse(const HostSeries &H, double T)
 {
     if (std::isinf(T)) return INFINITY;
     if (T <= 1.0) return 0.0;
-    double lo = 0.0, hi = 1e-300;
-    for (int it = 0; it < 2200 && series_F(H, hi) < T; ++it) hi *= 2.0;
-    for (int it = 0; it < 400; ++it) {
+    double bmin = INFINITY, bmax = 0.0, A = 0.0;
+    for (int q = 1; q < H.nq; ++q) { bmin = std::fmin(bmin, H.b[q]); bmax = std::fmax(bmax, H.b[q]); A += H.a[q]; }
+    const double L = std::log((T - H.a[0]) / A);
+    double lo = 0.0, hi = 0.0;
+    if (L > 0.0 && bmin > 0.0) {
+        lo = 0.999 * std::sqrt(L / bmax);
+        hi = 1.001 * std::sqrt(L / bmin);
+    }
+    if (!(hi > 0.0) || series_F(H, hi) < T) {          // fall back to doubling from a safe scale
+        hi = (bmin > 0.0 && std::isfinite(bmin)) ? 1.0 / std::sqrt(bmin) : 1.0;
+        for (int it = 0; it < 4096 && series_F(H, hi) < T; ++it) hi *= 2.0;
+        lo = 0.0;
+    }
+    if (series_F(H, lo) >= T) lo = 0.0;
+    for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
         if (series_F(H, mid) >= T) hi = mid; else lo = mid;
@@ -668,6 +756,42 @@ float strictly_above_f(double w)
     return f;
 }
 
+// G(u) = sum_{q>=1} a_q exp((b_q - b_1) u): the q >= 1 terms without the
+// common factor exp(b_1 u).
+double series_G(const HostSeries &H, double u)
+{
+    double acc = 0.0;
+    for (int q = 1; q < H.nq; ++q) acc += H.a[q] * std::exp((H.b[q] - H.b[1]) * u);
+    return acc;
+}
+
+// Chebyshev interpolant of G on [0, U] at degree deg (Chebyshev nodes of the
+// first kind); returns its largest relative error on a fine grid.
+double fit_G(const HostSeries &H, double U, int deg, double *coef)
+{
+    const int N = deg + 1;
+    double fv[RL0_MAXPOLY];
+    for (int j = 0; j < N; ++j) {
+        const double tj = std::cos(M_PI * (j + 0.5) / N);
+        fv[j] = series_G(H, 0.5 * (tj + 1.0) * U);
+    }
+    for (int k = 0; k < N; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc += fv[j] * std::cos(M_PI * k * (j + 0.5) / N);
+        coef[k] = (k == 0 ? 1.0 : 2.0) * acc / N;
+    }
+    double worst = 0.0;
+    for (int g = 0; g <= 2000; ++g) {
+        const double u = U * g / 2000.0, t = 2.0 * u / U - 1.0;
+        double b1 = 0.0, b2 = 0.0;
+        for (int k = N - 1; k >= 1; --k) { const double b0 = 2.0 * t * b1 - b2 + coef[k]; b2 = b1; b1 = b0; }
+        const double val = t * b1 - b2 + coef[0];
+        const double ref = series_G(H, u);
+        worst = std::fmax(worst, std::fabs(val - ref) / ref);
+    }
+    return worst;
+}
+
 Series to_device_series(const HostSeries &H, double cut)
 {
     Series S;
@@ -675,6 +799,21 @@ Series to_device_series(const HostSeries &H, double cut)
     S.nq = H.nq;
     for (int q = 0; q < H.nq; ++q) { S.a[q] = (float)H.a[q]; S.b[q] = (float)H.b[q]; }
     S.cut = round_up_f(cut);
+    // factored form when a short Chebyshev series reproduces G to 2e-9
+    const double U = (double)S.cut * (double)S.cut;
+    if (H.nq >= 2 && std::isfinite(U) && U > 0.0) {
+        double coef[RL0_MAXPOLY];
+        for (int deg = 2; deg < RL0_MAXPOLY; ++deg) {
+            if (fit_G(H, U, deg, coef) < 2e-9) {
+                S.use_poly = 1;
+                S.npoly = deg + 1;
+                S.b1 = (float)H.b[1];
+                S.inv_u2 = (float)(2.0 / U);
+                for (int k = 0; k <= deg; ++k) S.poly[k] = (float)coef[k];
+                break;
+            }
+        }
+    }
     return S;
 }
 
@@ -784,8 +923,8 @@ struct GraphEntry {
     std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
 
-// Kernels one decode graph launches: prologue (3), 6 per round, final check (1).
-int launches_per_decode(int nrounds) { return 3 + 6 * nrounds + 1; }
+// Kernels one decode graph launches: prologue (3), 5 per round, final check (2).
+int launches_per_decode(int nrounds) { return 3 + 5 * nrounds + 2; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -827,8 +966,7 @@ KArgs make_args(const rl0_expander *A)
 
 void launch_column_score(const KArgs &a, int dmax, int indicator, cudaStream_t s)
 {
-    const unsigned grid = rl0_div_up(a.n, 256);
-#define RL0_CS(D, I) k_column_score<D, I><<<grid, 256, 0, s>>>(a)
+#define RL0_CS(D, I) k_column_score<D, I><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
     if (dmax == 8) { if (indicator) RL0_CS(8, true); else RL0_CS(8, false); }
     else if (dmax == 16) { if (indicator) RL0_CS(16, true); else RL0_CS(16, false); }
     else { if (indicator) RL0_CS(32, true); else RL0_CS(32, false); }
@@ -843,30 +981,92 @@ void launch_round(const KArgs &a, int dmax, int indicator, cudaStream_t s)
     launch_column_score(a, dmax, indicator, s);
     k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
     k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rebuild<false><<<a.nchunks, 256, 0, s>>>(a);
-    k_rebuild<true><<<a.nchunks, 256, 0, s>>>(a);
+    k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+}
+
+// The round loop as a graph.  Normal decodes: prologue kernels, then a WHILE
+// conditional node whose body is one round (the accept kernel clears the
+// condition once the decode is done, so no kernel runs after convergence),
+// then the FP64 residual check.  Profile decodes: the rounds unrolled, with
+// event-record nodes around each kernel group (event nodes are not allowed in
+// a conditional body).
+int add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep, void *func,
+                    unsigned grid, unsigned block, KArgs *a, void **extra, int nextra)
+{
+    void *args[4] = {a, nullptr, nullptr, nullptr};
+    for (int i = 0; i < nextra; ++i) args[1 + i] = extra[i];
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = func;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.kernelParams = args;
+    CK(cudaGraphAddKernelNode(node, g, dep, ndep, &kp));
+    return RL0_OK;
 }
 
 int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int profile, GraphEntry *E)
 {
     GraphCache *gc = (GraphCache *)A->graph_cache;
-    const KArgs a = make_args(A);
+    KArgs a = make_args(A);
     cudaStream_t s = gc->capture_stream;
-    cudaGraph_t g = nullptr;
     E->nrounds = nrounds;
     E->dmax = dmax;
     E->indicator = indicator;
     E->profile = profile;
-    if (profile) {
-        E->events.resize(4 * nrounds + 1);
-        for (auto &ev : E->events) CK(cudaEventCreate(&ev));
+    cudaGraph_t g = nullptr;
+    if (!profile) {
+        CK(cudaGraphCreate(&g, 0));
+        int rc = RL0_OK;
+        do {
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+                rc = RL0_ERR_CUDA;
+                break;
+            }
+            a.cond = h;
+            a.has_cond = 1;
+            cudaGraphNode_t n0, n1, n2, nw, n3;
+            const float *nullsrc = nullptr;
+            int zero = 0, one = 1;
+            void *ex_rows[2] = {&nullsrc, &zero};
+            void *ex_start[2] = {&zero, &one};
+            if ((rc = add_kernel_node(g, &n0, nullptr, 0, (void *)k_zero_x, 2 * a.nsm, 256, &a, nullptr, 0))) break;
+            if ((rc = add_kernel_node(g, &n1, &n0, 1, (void *)k_rows_from, a.nchunks, RL0_ROWS_CHUNK, &a, ex_rows, 2)))
+                break;
+            if ((rc = add_kernel_node(g, &n2, &n1, 1, (void *)k_start, 1, 32, &a, ex_start, 2))) break;
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional, {0, 0, 0}, {}, 0};
+            std::memset((void *)&cp, 0, sizeof(cp));
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (cudaGraphAddNode(&nw, g, &n2, nullptr, 1, &cp) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) { rc = RL0_ERR_CUDA; break; }
+            launch_round(a, dmax, indicator, s);
+            k_accept<<<1, 1024, 0, s>>>(a);
+            cudaGraph_t body_out = nullptr;
+            if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
+            if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_l1, a.nchunks, RL0_ROWS_CHUNK, &a, nullptr, 0)))
+                break;
+            cudaGraphNode_t n4;
+            if ((rc = add_kernel_node(g, &n4, &n3, 1, (void *)k_final_sum, 1, 32, &a, nullptr, 0))) break;
+        } while (0);
+        if (rc) { cudaGetLastError(); cudaGraphDestroy(g); return rc; }
+        cudaError_t e = cudaGraphInstantiate(&E->exec, g, 0);
+        cudaGraphDestroy(g);
+        return rl0_cuda_err(e);
     }
+    E->events.resize(4 * nrounds + 1);
+    for (auto &ev : E->events) CK(cudaEventCreate(&ev));
     auto mark = [&](int idx) -> cudaError_t {
-        return profile ? cudaEventRecordWithFlags(E->events[idx], s, cudaEventRecordExternal) : cudaSuccess;
+        return cudaEventRecordWithFlags(E->events[idx], s, cudaEventRecordExternal);
     };
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, nullptr, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < nrounds && e == cudaSuccess; ++r) {
@@ -876,13 +1076,13 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
         if (e == cudaSuccess) e = mark(4 * r + 2);
         k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
-        k_rebuild<false><<<a.nchunks, 256, 0, s>>>(a);
-        k_rebuild<true><<<a.nchunks, 256, 0, s>>>(a);
+        k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
         if (e == cudaSuccess) e = mark(4 * r + 3);
         k_accept<<<1, 1024, 0, s>>>(a);
     }
     if (e == cudaSuccess) e = mark(4 * nrounds);
-    k_final_l1<<<a.nchunks, 256, 0, s>>>(a);
+    k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+    k_final_sum<<<1, 32, 0, s>>>(a);
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return rl0_cuda_err(e); }
     if (e2 != cudaSuccess) return rl0_cuda_err(e2);
@@ -897,6 +1097,16 @@ struct HostStage {
     DecodeState st;
     RoundThr thr[RL0_MAX_ROUNDS];
     RoundLog log[RL0_MAX_ROUNDS];
+};
+
+// Host tables of the last parameter set, reused when a decode repeats it.
+struct TableCache {
+    bool valid = false;
+    int64_t k = 0;
+    rl0_params p;
+    int nrounds = 0;
+    DecodeCtx ctx;
+    RoundThr thr[RL0_MAX_ROUNDS];
 };
 
 }  // namespace
@@ -936,7 +1146,17 @@ int rl0_workspace_alloc(rl0_expander *A)
     if (!gc) return RL0_ERR_ALLOC;
     A->graph_cache = gc;
     e = cudaStreamCreateWithFlags(&gc->capture_stream, cudaStreamNonBlocking);
-    return rl0_cuda_err(e);
+    if (e != cudaSuccess) return rl0_cuda_err(e);
+    cudaEvent_t *ev = new (std::nothrow) cudaEvent_t[2];
+    if (!ev) return RL0_ERR_ALLOC;
+    A->events = ev;
+    e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e != cudaSuccess) return rl0_cuda_err(e);
+    TableCache *tc = new (std::nothrow) TableCache;
+    if (!tc) return RL0_ERR_ALLOC;
+    A->table_cache = tc;
+    return RL0_OK;
 }
 
 void rl0_workspace_free(rl0_expander *A)
@@ -952,6 +1172,17 @@ void rl0_workspace_free(rl0_expander *A)
         delete gc;
         A->graph_cache = nullptr;
     }
+    if (A->events) {
+        cudaEvent_t *ev = (cudaEvent_t *)A->events;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        delete[] ev;
+        A->events = nullptr;
+    }
+    if (A->table_cache) {
+        delete (TableCache *)A->table_cache;
+        A->table_cache = nullptr;
+    }
     void *ptrs[] = {w.rz[0], w.rz[1], w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt, w.l1part,
                     w.hk_scratch, w.st, w.ctx, w.thr, w.rlog, w.final_part};
     for (void *p : ptrs) if (p) cudaFree(p);
@@ -961,6 +1192,32 @@ void rl0_workspace_free(rl0_expander *A)
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+static bool same_params(const rl0_params &a, const rl0_params &b)
+{
+    return a.sigma_s == b.sigma_s && a.sigma_n == b.sigma_n && a.quantised == b.quantised && a.c == b.c &&
+           a.alpha == b.alpha && a.ell == b.ell && a.scorer == b.scorer && a.mlp == b.mlp &&
+           a.mlp_threshold == b.mlp_threshold && a.max_rounds == b.max_rounds && a.noiseless_tol == b.noiseless_tol;
+}
+
+static void cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr)
+{
+    TableCache *tc = (TableCache *)A->table_cache;
+    if (tc && tc->valid && tc->k == k && tc->nrounds == R.nrounds && same_params(tc->p, R.p)) {
+        *ctx = tc->ctx;
+        std::memcpy(thr, tc->thr, R.nrounds * sizeof(RoundThr));
+        return;
+    }
+    fill_tables(A, k, R, ctx, thr, R.nrounds);
+    if (tc) {
+        tc->valid = true;
+        tc->k = k;
+        tc->p = R.p;
+        tc->nrounds = R.nrounds;
+        tc->ctx = *ctx;
+        std::memcpy(tc->thr, thr, R.nrounds * sizeof(RoundThr));
+    }
+}
+
 static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
                          float *xhat_dev, rl0_stats *stats, cudaStream_t s)
 {
@@ -969,7 +1226,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     int rc = resolve(A, k, params, &R);
     if (rc) return rc;
     HostStage *H = (HostStage *)A->host_pinned;
-    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    cached_tables(A, k, R, &H->ctx, H->thr);
     H->ctx.y = y_dev;
     H->ctx.x = xhat_dev;
     H->ctx.want_log = 1;
@@ -994,40 +1251,28 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         gc->entries.push_back(fresh);
         E = &gc->entries.back();
     }
-    cudaGraphExec_t exec = E->exec;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (stats) {
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        CK(cudaEventRecord(e0, s));
-    }
-    CK(cudaGraphLaunch(exec, s));
-    if (stats) CK(cudaEventRecord(e1, s));
+    cudaEvent_t *ev = (cudaEvent_t *)A->events;
+    if (stats) CK(cudaEventRecord(ev[0], s));
+    CK(cudaGraphLaunch(E->exec, s));
+    if (stats) CK(cudaEventRecord(ev[1], s));
     CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
-    const int nchunks = (int)rl0_div_up(A->m, RL0_ROWS_CHUNK);
-    std::vector<double> part(nchunks);
-    CK(cudaMemcpyAsync(part.data(), w.final_part, nchunks * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(H->log, w.rlog, R.nrounds * sizeof(RoundLog), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
     if (stats) {
         float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        double l1 = 0.0;
-        for (double v : part) l1 += v;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
         std::memset(stats, 0, sizeof(*stats));
         stats->rounds = H->st.rounds_run;
         stats->accepted_rounds = H->st.accepted_rounds;
         stats->converged = H->st.converged;
         stats->status = H->st.status;
-        stats->support_size = H->st.shat_count;
-        stats->final_l1 = l1;
+        stats->support_size = H->st.nnz;
+        stats->final_l1 = H->st.final_l1;
         stats->ms = ms;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = launches_per_decode(R.nrounds);
+        stats->launches = launches_per_decode(prof ? R.nrounds : H->st.rounds_run);
         if (prof) {
             float acc[4] = {0, 0, 0, 0};
             for (int r = 0; r < R.nrounds; ++r)
@@ -1129,7 +1374,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     const KArgs a = make_args(A);
     k_copy_f<<<2 * a.nsm, 256, 0, s>>>(xhat_dev, xp_dev, a.n);
-    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, rhat_dev, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0);
     k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
     k_list_count_from_support<<<1, 32, 0, s>>>(a);
@@ -1280,28 +1525,26 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
 
     const int dmax = dmax_of(A->d);
     k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rows_from<<<a.nchunks, 256, 0, s>>>(a, nullptr, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     for (int r = 0; r < R.nrounds; ++r) {
         launch_round(a, dmax, R.indicator, s);
         k_accept<<<1, 1024, 0, s>>>(a);
     }
-    k_final_l1<<<a.nchunks, 256, 0, s>>>(a);
+    k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+    k_final_sum<<<1, 32, 0, s>>>(a);
     CK(cudaGetLastError());
-    double part[RL0_STATIC_CHUNKS];
     CK(cudaMemcpyAsync(&H->st, base + L.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(part, base + L.final_part, sizeof(double) * a.nchunks, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
     if (stats) {
-        double l1 = 0.0;
-        for (int c = 0; c < a.nchunks; ++c) l1 += part[c];
+        const double l1 = H->st.final_l1;
         std::memset(stats, 0, sizeof(*stats));
         stats->rounds = H->st.rounds_run;
         stats->accepted_rounds = H->st.accepted_rounds;
         stats->converged = H->st.converged;
         stats->status = H->st.status;
-        stats->support_size = H->st.shat_count;
+        stats->support_size = H->st.nnz;
         stats->final_l1 = l1;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
