@@ -149,6 +149,28 @@ struct rl0_expander {
 #define RL0_STATIC_MAX_N 65536
 #define RL0_STATIC_MAX_M 32768
 
+// ---- host tables (rl0_tables.cu) ------------------------------------------
+namespace rl0 {
+struct HostSeries {
+    int nq;
+    double a[RL0_MAXQ], b[RL0_MAXQ];
+};
+struct Resolved {
+    rl0_params p;
+    int nrounds;
+    int indicator;
+    double stop_level, stop_rel;
+};
+HostSeries make_series(double lam, double s2, double vn, int ell);
+double series_F(const HostSeries &H, double w);
+float series_threshold_up(const HostSeries &H, double T);
+float series_threshold_down(const HostSeries &H, double T);
+Series to_device_series(const HostSeries &H);
+double default_c(int quantised, double delta, double rho);
+int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolved *R);
+void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr);
+}  // namespace rl0
+
 // ---- helpers shared by translation units -------------------------------
 int rl0_set_device_of(const rl0_expander *A);
 int rl0_cuda_err(cudaError_t e);

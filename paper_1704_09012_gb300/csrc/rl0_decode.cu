@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "rl0_common.cuh"
+#include "rl0_device.cuh"
 
 #define CK(call)                                          \
     do {                                                  \
@@ -51,48 +52,6 @@ struct KArgs {
     cudaGraphConditionalHandle cond;   // while-loop condition of the round graph
     int has_cond;
 };
-
-// ---------------------------------------------------------------------------
-// Posterior evaluation in FP32: 1/p_breve(w) = sum_q a_q exp(b_q w^2).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float series_eval(const Series &S, float w)
-{
-    if (w == 0.0f) return 1.0f;                 // p_breve(0) = 1 exactly
-    if (fabsf(w) > S.cut) return 0.0f;          // below 2^-40
-    const float u = w * w;
-    float acc;
-    if (S.use_poly) {
-        const float t = fmaf(u, S.inv_u2, -1.0f);
-        const float t2 = 2.0f * t;
-        float b1 = 0.0f, b2 = 0.0f;
-        for (int k = S.npoly - 1; k >= 1; --k) {   // Clenshaw recurrence
-            const float b0 = fmaf(t2, b1, S.poly[k] - b2);
-            b2 = b1;
-            b1 = b0;
-        }
-        const float G = fmaf(t, b1, S.poly[0] - b2);
-        acc = fmaf(expf(S.b1 * u), G, S.a[0]);
-    } else {
-        acc = S.a[0];
-        for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * u);
-    }
-    return 1.0f / acc;
-}
-
-__device__ __forceinline__ double block_sum_f64(double v, double *sh)
-{
-    // fixed-shape tree over the block: deterministic for a given blockDim
-    const int t = threadIdx.x;
-    sh[t] = v;
-    __syncthreads();
-    for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
-        if (t < off) sh[t] += sh[t + off];
-        __syncthreads();
-    }
-    const double r = sh[0];
-    __syncthreads();
-    return r;
-}
 
 // r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
 // chunk (one row per thread, blockDim = RL0_ROWS_CHUNK).
@@ -187,8 +146,7 @@ __global__ void k_list_count_from_support(KArgs a)
 // order, get the exact n_e, omega and l1 test from residuals kept in shared
 // memory, in the same order of operations for every launch shape.
 // ---------------------------------------------------------------------------
-// Threads per CTA of the column kernel: the shared candidate arrays scale
-// with DMAX x threads and must stay within the 48 KB of static shared memory.
+// Threads per CTA of the column kernel (its shared arrays scale with DMAX).
 template <int DMAX> struct ColBlock { static constexpr int value = DMAX <= 8 ? 256 : (DMAX <= 16 ? 128 : 64); };
 
 template <int DMAX, bool IND>
@@ -197,11 +155,10 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     constexpr int NT = ColBlock<DMAX>::value;
     __shared__ Series s_pe;
     __shared__ float s_r[DMAX][NT];           // residuals of columns with candidates
-    __shared__ float s_score[DMAX][NT];       // n_e - n_z of passing candidates
-    __shared__ float s_w[DMAX][NT];           // omega of passing candidates
     __shared__ float s_nz[NT], s_rhs[NT];
-    __shared__ unsigned s_pass[NT];           // passing anchors of each column (bit per slot)
-    __shared__ unsigned short s_q[NT * DMAX]; // candidate queue: (column lane << 5) | slot
+    __shared__ unsigned short s_q[NT];        // this pass's queue: (column lane << 5) | slot
+    __shared__ float s_score[NT], s_w[NT];
+    __shared__ unsigned char s_ok[NT];
     __shared__ int s_nq;
     const DecodeState *st = a.st;
     if (st->done) return;
@@ -215,10 +172,9 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         s_nq = 0;
         if (!IND) s_pe = ctx->pe;
     }
-    s_pass[tid] = 0u;
     __syncthreads();
     const int n = a.n, d = a.d;
-    const int j = blockIdx.x * blockDim.x + tid;
+    const int j = blockIdx.x * NT + tid;
     const bool active = j < n;
 
     float r[DMAX];
@@ -234,78 +190,42 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             rhs += fabsf(v.x);
         }
     }
-    const float reach = IND ? th.te : s_pe.cut;
-    unsigned cand = 0;
-    if (active) {
-        unsigned amask = 0;
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s)
-            if (s < d && fabsf(r[s]) >= th.ta) amask |= 1u << s;
-        if (amask) {
-            unsigned nm[DMAX];
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s) nm[s] = 0u;
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s) {
-#pragma unroll
-                for (int l = s + 1; l < DMAX; ++l) {
-                    if (l < d && fabsf(r[s] - r[l]) <= reach) {
-                        nm[s] |= 1u << l;
-                        nm[l] |= 1u << s;
-                    }
-                }
-            }
-            const float need = IND ? alpha : alpha - 1e-3f;
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s)
-                if (((amask >> s) & 1u) && (1.0f + (float)__popc(nm[s])) - nz >= need) cand |= 1u << s;
-        }
-    }
+    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, alpha) : 0u;
     if (cand) {
 #pragma unroll
         for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
         s_nz[tid] = nz;
         s_rhs[tid] = rhs;
-        int base = atomicAdd(&s_nq, __popc(cand));
-        for (unsigned c = cand; c; c &= c - 1u) s_q[base++] = (unsigned short)((tid << 5) | (__ffs(c) - 1));
     }
-    __syncthreads();
-    // exact scores of the queued (column, anchor) pairs, spread over the whole CTA
-    const int nq = s_nq;
-    for (int e = tid; e < nq; e += NT) {
-        const int owner = s_q[e] >> 5, s = s_q[e] & 31;
-        const float rs = s_r[s][owner];
-        float ne = 0.0f, num = 0.0f;
-#pragma unroll 1
-        for (int l = 0; l < d; ++l) {
-            const float rl = s_r[l][owner];
-            const float q = IND ? (fabsf(rs - rl) <= th.te ? 1.0f : 0.0f) : series_eval(s_pe, rs - rl);
-            ne += q;
-            num += rl * q;
-        }
-        const float w = num / ne;
-        float lhs = 0.0f;
-#pragma unroll 1
-        for (int l = 0; l < d; ++l) lhs += fabsf(s_r[l][owner] - w);
-        const float score = ne - s_nz[owner];
-        if (lhs <= s_rhs[owner] && score >= alpha) {
-            s_score[s][owner] = score;
-            s_w[s][owner] = w;
-            atomicOr(&s_pass[owner], 1u << s);
-        }
-    }
-    __syncthreads();
-    // the best passing anchor of the column: largest n_e - n_z, ties to the lowest slot
+    // candidates are scored by the whole CTA, one per column per pass, each
+    // column's candidates in slot order
     int best = -1;
     float bscore = 0.0f, bw = 0.0f;
-    for (unsigned pm = s_pass[tid]; pm; pm &= pm - 1u) {
-        const int s = __ffs(pm) - 1;
-        const float sc = s_score[s][tid];
-        if (best < 0 || sc > bscore) {
-            best = s;
-            bscore = sc;
-            bw = s_w[s][tid];
+    while (__syncthreads_or(cand != 0u)) {
+        int my = -1, ms = 0;
+        if (cand) {
+            ms = __ffs(cand) - 1;
+            cand &= cand - 1u;
+            my = atomicAdd(&s_nq, 1);
+            s_q[my] = (unsigned short)((tid << 5) | ms);
         }
+        __syncthreads();
+        const int nq = s_nq;
+        for (int e = tid; e < nq; e += NT) {
+            const int owner = s_q[e] >> 5, s = s_q[e] & 31;
+            float sc, w;
+            s_ok[e] = score_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe, s_nz[owner], s_rhs[owner], alpha,
+                                        &sc, &w) ? 1 : 0;
+            s_score[e] = sc;
+            s_w[e] = w;
+        }
+        __syncthreads();
+        if (my >= 0 && s_ok[my] && (best < 0 || s_score[my] > bscore)) {
+            best = ms;
+            bscore = s_score[my];
+            bw = s_w[my];
+        }
+        if (tid == 0) s_nq = 0;
     }
     const bool pass = best >= 0;
     float old = 0.0f, nv = 0.0f;
@@ -352,89 +272,18 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
 // passes of at most 11 bits, then zero (and log) everything below it.
 // ---------------------------------------------------------------------------
 #define HK_THREADS 1024
-#define HK_BINS 2048
-
-__device__ __forceinline__ unsigned long long hk_key(float v, int j)
-{
-    return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (unsigned long long)(0xffffffffu - (unsigned)j);
-}
 
 __global__ void __launch_bounds__(HK_THREADS) k_hk_select(KArgs a)
 {
-    __shared__ unsigned hist[HK_BINS];
+    __shared__ HkShared sm;
     __shared__ unsigned suf[HK_THREADS];
-    __shared__ unsigned long long s_prefix;
-    __shared__ unsigned s_need;
     DecodeState *st = a.st;
     if (st->done || st->upd_count == 0) return;
-    const long long k = a.ctx->k;
-    const float *x = a.ctx->x;
-    const unsigned total = st->list_count;
-    const int t = threadIdx.x;
-
     // |supp x'| is known from the counters: nothing to do when it is at most k
     const long long nnz = (long long)st->nnz + st->nnz_delta;
+    const long long k = a.ctx->k;
     if (nnz <= k) return;
-    for (unsigned e = t; e < total; e += HK_THREADS) {
-        const int j = a.list[e];
-        const float v = x[j];
-        a.hkkey[e] = (v != 0.0f) ? hk_key(v, j) : 0ull;
-    }
-    __syncthreads();
-    if (t == 0) { s_prefix = 0ull; s_need = (unsigned)k; }
-    __syncthreads();
-    const int shifts[6] = {52, 41, 30, 19, 8, 0};
-    const int widths[6] = {11, 11, 11, 11, 11, 8};
-    for (int p = 0; p < 6; ++p) {
-        const int sh = shifts[p], wd = widths[p];
-        const unsigned nb = 1u << wd;
-        for (unsigned b = t; b < HK_BINS; b += HK_THREADS) hist[b] = 0;
-        __syncthreads();
-        const unsigned long long prefix = s_prefix;
-        const unsigned need = s_need;
-        for (unsigned e = t; e < total; e += HK_THREADS) {
-            const unsigned long long key = a.hkkey[e];
-            if (key != 0ull && (key >> (sh + wd)) == prefix)
-                atomicAdd(&hist[(unsigned)(key >> sh) & (nb - 1u)], 1u);
-        }
-        __syncthreads();
-        // inclusive suffix sums over bins, two bins per thread (high bins first)
-        const unsigned b0 = nb - 1 - 2 * t, b1 = b0 - 1;
-        const unsigned own = (2u * t < nb) ? hist[b0] + (2u * t + 1 < nb ? hist[b1] : 0u) : 0u;
-        suf[t] = own;
-        __syncthreads();
-        for (int off = 1; off < HK_THREADS; off <<= 1) {
-            const unsigned v = (t >= off) ? suf[t - off] : 0u;
-            __syncthreads();
-            suf[t] += v;
-            __syncthreads();
-        }
-        if (2u * t < nb) {
-            const unsigned before = suf[t] - own;           // count in bins above b0
-            const unsigned at_b0 = before + hist[b0];
-            if (before < need && at_b0 >= need) {
-                s_prefix = (prefix << wd) | b0;
-                s_need = need - before;
-            } else if (2u * t + 1 < nb && at_b0 < need && suf[t] >= need) {
-                s_prefix = (prefix << wd) | b1;
-                s_need = need - at_b0;
-            }
-        }
-        __syncthreads();
-    }
-    const unsigned long long kth = s_prefix;            // the k-th largest key
-    for (unsigned e = t; e < total; e += HK_THREADS) {
-        const unsigned long long key = a.hkkey[e];
-        if (key != 0ull && key < kth) {
-            const int j = a.list[e];
-            float *xm = a.ctx->x;
-            UndoEntry u;
-            u.j = j;
-            u.old = xm[j];
-            xm[j] = 0.0f;
-            a.dlog[atomicAdd(&st->drop_count, 1u)] = u;
-        }
-    }
+    cta_hk_select<HK_THREADS>(a.list, st->list_count, a.ctx->x, k, a.hkkey, a.dlog, &st->drop_count, sm, suf);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +310,6 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a)
     }
 }
 
-#define RL0_CSWAP(i, j) { const int lo_ = min(js[i], js[j]), hi_ = max(js[i], js[j]); js[i] = lo_; js[j] = hi_; }
 
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
 {
@@ -486,12 +334,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
                 int js[RL0_BUCKET];
 #pragma unroll
                 for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
-                // ascending column order (Batcher's 19-comparator network)
-                RL0_CSWAP(0, 1) RL0_CSWAP(2, 3) RL0_CSWAP(4, 5) RL0_CSWAP(6, 7)
-                RL0_CSWAP(0, 2) RL0_CSWAP(1, 3) RL0_CSWAP(4, 6) RL0_CSWAP(5, 7)
-                RL0_CSWAP(1, 2) RL0_CSWAP(5, 6) RL0_CSWAP(0, 4) RL0_CSWAP(1, 5)
-                RL0_CSWAP(2, 6) RL0_CSWAP(3, 7) RL0_CSWAP(2, 4) RL0_CSWAP(3, 5)
-                RL0_CSWAP(1, 2) RL0_CSWAP(3, 4) RL0_CSWAP(5, 6)
+                sort8(js);                              // ascending column order
 #pragma unroll
                 for (int q = 0; q < RL0_BUCKET; ++q)
                     if (q < c) sum += x[js[q]];
@@ -645,277 +488,9 @@ __global__ void k_extract_r(KArgs a, float *rp, int use_candidate_always)
 // ---------------------------------------------------------------------------
 // Host: posterior coefficients and thresholds in FP64.
 // ---------------------------------------------------------------------------
+using rl0::Resolved;
+
 namespace {
-
-struct HostSeries {
-    int nq;
-    double a[RL0_MAXQ], b[RL0_MAXQ];
-};
-
-// Eq. (pz_approx) (lam = d rho, vn = s_n^2) or Eq. (pe_approx) (lam = 2 d rho,
-// vn = 2 s_n^2): terms q = 0..ell with weight lam^q/q! and variance
-// q s_s^2 + vn, and the tail R(ell) = sum_{q>ell} lam^q/q! with the
-// variance-matched v = (s_s^2 lam R(ell-1) + vn R(ell)) / R(ell).  Dividing
-// numerator and denominator by the noise density gives
-//   p(0)/p(w) = sum_terms c_t sqrt(vn/v_t) exp(w^2 (1/(2 vn) - 1/(2 v_t))) / D,
-// with D the same sum at w = 0 (the maximum of p is at 0).
-HostSeries make_series(double lam, double s2, double vn, int ell)
-{
-    double wt[RL0_MAXQ], var[RL0_MAXQ];
-    int nt = 0;
-    double term = 1.0;
-    for (int q = 0; q <= ell; ++q) {
-        if (q > 0) term *= lam / q;
-        wt[nt] = term;
-        var[nt] = q * s2 + vn;
-        ++nt;
-    }
-    // tails R(ell) and R(ell - 1), summed directly
-    double tq = term, Rl = 0.0;
-    for (int q = ell + 1; q < ell + 4000; ++q) {
-        tq *= lam / q;
-        Rl += tq;
-        if (tq == 0.0 || (q > lam && tq < Rl * 1e-18)) break;
-    }
-    const double Rlm1 = Rl + term;               // adds the q = ell term
-    if (Rl > 0.0) {
-        wt[nt] = Rl;
-        var[nt] = (s2 * lam * Rlm1 + vn * Rl) / Rl;
-        ++nt;
-    }
-    HostSeries H;
-    H.nq = nt;
-    double D = 0.0;
-    for (int q = 0; q < nt; ++q) D += wt[q] * std::sqrt(vn / var[q]);
-    for (int q = 0; q < nt; ++q) {
-        H.a[q] = wt[q] * std::sqrt(vn / var[q]) / D;
-        H.b[q] = 0.5 / vn - 0.5 / var[q];
-    }
-    H.b[0] = 0.0;
-    return H;
-}
-
-double series_F(const HostSeries &H, double w)
-{
-    double acc = 0.0;
-    for (int q = 0; q < H.nq; ++q) acc += H.a[q] * std::exp(H.b[q] * w * w);
-    return acc;
-}
-
-// Smallest w >= 0 with F(w) >= T (F increasing in |w|); +inf for T = inf.
-// Every q >= 1 term has b_1 <= b_q <= b_max, so with A = 1 - a_0,
-//   a_0 + A exp(b_1 w^2) <= F(w) <= a_0 + A exp(b_max w^2),
-// which brackets the root; bisection then runs to adjacent doubles.
-double series_inverse(const HostSeries &H, double T)
-{
-    if (std::isinf(T)) return INFINITY;
-    if (T <= 1.0) return 0.0;
-    double bmin = INFINITY, bmax = 0.0, A = 0.0;
-    for (int q = 1; q < H.nq; ++q) { bmin = std::fmin(bmin, H.b[q]); bmax = std::fmax(bmax, H.b[q]); A += H.a[q]; }
-    const double L = std::log((T - H.a[0]) / A);
-    double lo = 0.0, hi = 0.0;
-    if (L > 0.0 && bmin > 0.0) {
-        lo = 0.999 * std::sqrt(L / bmax);
-        hi = 1.001 * std::sqrt(L / bmin);
-    }
-    if (!(hi > 0.0) || series_F(H, hi) < T) {          // fall back to doubling from a safe scale
-        hi = (bmin > 0.0 && std::isfinite(bmin)) ? 1.0 / std::sqrt(bmin) : 1.0;
-        for (int it = 0; it < 4096 && series_F(H, hi) < T; ++it) hi *= 2.0;
-        lo = 0.0;
-    }
-    if (series_F(H, lo) >= T) lo = 0.0;
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (series_F(H, mid) >= T) hi = mid; else lo = mid;
-    }
-    return hi;
-}
-
-float round_up_f(double w)
-{
-    if (std::isinf(w)) return INFINITY;
-    float f = (float)w;
-    if ((double)f < w) f = std::nextafter(f, INFINITY);
-    return f;
-}
-
-float round_down_f(double w)
-{
-    if (std::isinf(w)) return INFINITY;
-    float f = (float)w;
-    if ((double)f > w) f = std::nextafter(f, -INFINITY);
-    return f;
-}
-
-// Smallest float strictly above w.
-float strictly_above_f(double w)
-{
-    float f = round_up_f(w);
-    if ((double)f == w) f = std::nextafter(f, INFINITY);
-    return f;
-}
-
-// G(u) = sum_{q>=1} a_q exp((b_q - b_1) u): the q >= 1 terms without the
-// common factor exp(b_1 u).
-double series_G(const HostSeries &H, double u)
-{
-    double acc = 0.0;
-    for (int q = 1; q < H.nq; ++q) acc += H.a[q] * std::exp((H.b[q] - H.b[1]) * u);
-    return acc;
-}
-
-// Chebyshev interpolant of G on [0, U] at degree deg (Chebyshev nodes of the
-// first kind); returns its largest relative error on a fine grid.
-double fit_G(const HostSeries &H, double U, int deg, double *coef)
-{
-    const int N = deg + 1;
-    double fv[RL0_MAXPOLY];
-    for (int j = 0; j < N; ++j) {
-        const double tj = std::cos(M_PI * (j + 0.5) / N);
-        fv[j] = series_G(H, 0.5 * (tj + 1.0) * U);
-    }
-    for (int k = 0; k < N; ++k) {
-        double acc = 0.0;
-        for (int j = 0; j < N; ++j) acc += fv[j] * std::cos(M_PI * k * (j + 0.5) / N);
-        coef[k] = (k == 0 ? 1.0 : 2.0) * acc / N;
-    }
-    double worst = 0.0;
-    for (int g = 0; g <= 2000; ++g) {
-        const double u = U * g / 2000.0, t = 2.0 * u / U - 1.0;
-        double b1 = 0.0, b2 = 0.0;
-        for (int k = N - 1; k >= 1; --k) { const double b0 = 2.0 * t * b1 - b2 + coef[k]; b2 = b1; b1 = b0; }
-        const double val = t * b1 - b2 + coef[0];
-        const double ref = series_G(H, u);
-        worst = std::fmax(worst, std::fabs(val - ref) / ref);
-    }
-    return worst;
-}
-
-Series to_device_series(const HostSeries &H, double cut)
-{
-    Series S;
-    std::memset(&S, 0, sizeof(S));
-    S.nq = H.nq;
-    for (int q = 0; q < H.nq; ++q) { S.a[q] = (float)H.a[q]; S.b[q] = (float)H.b[q]; }
-    S.cut = round_up_f(cut);
-    // factored form when a short Chebyshev series reproduces G to 2e-9
-    const double U = (double)S.cut * (double)S.cut;
-    if (H.nq >= 2 && std::isfinite(U) && U > 0.0) {
-        double coef[RL0_MAXPOLY];
-        for (int deg = 2; deg < RL0_MAXPOLY; ++deg) {
-            if (fit_G(H, U, deg, coef) < 2e-9) {
-                S.use_poly = 1;
-                S.npoly = deg + 1;
-                S.b1 = (float)H.b[1];
-                S.inv_u2 = (float)(2.0 / U);
-                for (int k = 0; k <= deg; ++k) S.poly[k] = (float)coef[k];
-                break;
-            }
-        }
-    }
-    return S;
-}
-
-// Eqs. (finetune_c_quant), (finetune_c_cont).
-double default_c(int quantised, double delta, double rho)
-{
-    if (quantised) {
-        if (delta <= 0.05) return 0.01;
-        if (rho <= 0.1) return 0.05;
-        if (rho <= 0.2) return 0.075;
-        return 0.1;
-    }
-    return delta <= 0.05 ? 0.01 : 0.025;
-}
-
-struct Resolved {
-    rl0_params p;
-    int nrounds;
-    int indicator;
-    double stop_level, stop_rel;
-};
-
-int resolve(const rl0_expander *A, int64_t k, const rl0_params *in, Resolved *R)
-{
-    rl0_params p;
-    std::memset(&p, 0, sizeof(p));
-    if (in) p = *in;
-    if (p.sigma_s == 0.0) p.sigma_s = 1.0;
-    if (!(p.sigma_s > 0.0) || !(p.sigma_n >= 0.0) || !std::isfinite(p.sigma_n) || !std::isfinite(p.sigma_s))
-        return RL0_ERR_INVALID_ARG;
-    if (p.adaptive_k) return RL0_ERR_UNSUPPORTED;
-    if (k < 1 || k > A->n) return RL0_ERR_INVALID_ARG;
-    if (p.c == 0.0) p.c = default_c(p.quantised, (double)A->m / (double)A->n, (double)k / (double)A->m);
-    if (!(p.c > 0.0 && p.c <= 1.0)) return RL0_ERR_INVALID_ARG;
-    if (p.alpha == 0.0) p.alpha = p.quantised ? (double)(A->d / 2 + 1) : 0.5 * A->d;
-    if (!(p.alpha > 0.0)) return RL0_ERR_INVALID_ARG;
-    if (p.ell == 0) p.ell = 4;
-    if (p.ell < 1 || p.ell > RL0_MAXQ - 2) return RL0_ERR_INVALID_ARG;
-    if (p.noiseless_tol == 0.0) p.noiseless_tol = 1e-5;
-    if (!(p.noiseless_tol > 0.0)) return RL0_ERR_INVALID_ARG;
-    if (p.scorer != 0 && p.scorer != 1) return RL0_ERR_INVALID_ARG;
-    if (p.scorer == 1) return RL0_ERR_UNSUPPORTED;
-    int nr = (int)std::ceil(1.0 / p.c - 1e-9);
-    if (p.max_rounds > 0 && p.max_rounds < nr) nr = p.max_rounds;
-    if (nr > RL0_MAX_ROUNDS) return RL0_ERR_UNSUPPORTED;
-    if (p.profile != 0 && p.profile != 1) return RL0_ERR_INVALID_ARG;
-    R->p = p;
-    R->nrounds = nr;
-    R->indicator = p.quantised || p.sigma_n == 0.0;
-    R->stop_level = (p.sigma_n > 0.0) ? (double)A->m * p.sigma_n * std::sqrt(2.0 / M_PI) : 0.0;
-    R->stop_rel = (p.sigma_n > 0.0) ? 0.0 : p.noiseless_tol;
-    return RL0_OK;
-}
-
-// Fill the device context and the per-round thresholds (host copies).
-void fill_tables(const rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr)
-{
-    const rl0_params &p = R.p;
-    const double rho = (double)k / (double)A->m;
-    const double s2 = p.sigma_s * p.sigma_s, n2 = p.sigma_n * p.sigma_n;
-    std::memset(ctx, 0, sizeof(*ctx));
-    ctx->k = k;
-    ctx->alpha = (float)p.alpha;
-    ctx->nrounds = R.nrounds;
-    ctx->quantised = p.quantised;
-    ctx->indicator = R.indicator;
-    ctx->stop_level = R.stop_level;
-    ctx->stop_rel = R.stop_rel;
-    ctx->scorer = p.scorer;
-    ctx->mlp = p.mlp;
-    ctx->mlp_threshold = (float)(p.mlp_threshold == 0.0 ? 0.5 : p.mlp_threshold);
-    HostSeries hz, he;
-    if (p.sigma_n > 0.0) {
-        hz = make_series(A->d * rho, s2, n2, p.ell);
-        he = make_series(2.0 * A->d * rho, s2, 2.0 * n2, p.ell);
-        const double tiny = std::ldexp(1.0, 40);
-        ctx->pz = to_device_series(hz, series_inverse(hz, tiny));
-        ctx->pe = to_device_series(he, series_inverse(he, tiny));
-    }
-    for (int r = 0; r < nthr; ++r) {
-        const double t = 1.0 - r * p.c;
-        RoundThr T;
-        T.t = (float)t;
-        if (p.sigma_n == 0.0) {
-            // p_breve is the indicator of |w| <= tol
-            const float tol_dn = round_down_f(p.noiseless_tol);
-            T.ta = strictly_above_f(p.noiseless_tol);       // p_z = 0  <=> |r| > tol
-            T.te = tol_dn;                                  // p_e >= t <=> |D| <= tol (t in (0, 1])
-            T.tz = (p.quantised && t >= 1.0) ? INFINITY : tol_dn;   // p_z >= 1 - t
-        } else {
-            // anchor: p_z(r) <= 1 - t <=> F_z(r) >= 1/(1-t);  q_z: p_z(r) >= 1 - t <=> F_z(r) <= 1/(1-t)
-            const double Tz = (t >= 1.0) ? INFINITY : 1.0 / (1.0 - t);
-            const double wz = series_inverse(hz, Tz);
-            T.ta = round_up_f(wz);
-            T.tz = round_down_f(wz);
-            // q_e (quantised): p_e(D) >= t <=> F_e(D) <= 1/t
-            const double we = series_inverse(he, 1.0 / t);
-            T.te = round_down_f(we);
-        }
-        thr[r] = T;
-    }
-}
 
 struct GraphEntry {
     int nrounds, dmax, indicator, profile;
@@ -1207,7 +782,7 @@ static void cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeC
         std::memcpy(thr, tc->thr, R.nrounds * sizeof(RoundThr));
         return;
     }
-    fill_tables(A, k, R, ctx, thr, R.nrounds);
+    rl0::fill_tables(A->m, A->d, k, R, ctx, thr, R.nrounds);
     if (tc) {
         tc->valid = true;
         tc->k = k;
@@ -1223,8 +798,10 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
 {
     rl0_expander *A = const_cast<rl0_expander *>(Ac);
     Resolved R;
-    int rc = resolve(A, k, params, &R);
+    int rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
+    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
+    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     HostStage *H = (HostStage *)A->host_pinned;
     cached_tables(A, k, R, &H->ctx, H->thr);
     H->ctx.y = y_dev;
@@ -1356,14 +933,15 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     Resolved R;
-    rc = resolve(A, k, params, &R);
+    rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
+    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     if (round_index >= RL0_MAX_ROUNDS) return RL0_ERR_INVALID_ARG;
     R.nrounds = round_index + 1;
     R.stop_level = -1.0;                          // never "converged" here
     R.stop_rel = 0.0;
     HostStage *H = (HostStage *)A->host_pinned;
-    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    rl0::fill_tables(A->m, A->d, k, R, &H->ctx, H->thr, R.nrounds);
     H->ctx.y = y_dev;
     H->ctx.x = xp_dev;
     H->ctx.want_log = 0;
@@ -1399,13 +977,6 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     return RL0_OK;
 }
 
-extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const float *const *y_dev,
-                                  const int64_t *k, const rl0_params *params, float *const *xhat_dev,
-                                  rl0_stats *stats, void *cuda_stream)
-{
-    (void)count; (void)A; (void)y_dev; (void)k; (void)params; (void)xhat_dev; (void)stats; (void)cuda_stream;
-    return RL0_ERR_UNSUPPORTED;
-}
 
 // ---------------------------------------------------------------------------
 // rl0_decode_static: the same decode with no allocation at all.
@@ -1485,8 +1056,9 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     int rc = rl0_set_device_of(A);
     if (rc) return rc;
     Resolved R;
-    rc = resolve(A, k, params, &R);
+    rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
+    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     unsigned char *base = nullptr;
     rc = static_scratch_base(A->device, &base);
     if (rc) return rc;
@@ -1512,7 +1084,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     // Per-call tables go through the expander's pinned staging block, which was
     // set up when the expander was created.
     HostStage *H = (HostStage *)A->host_pinned;
-    fill_tables(A, k, R, &H->ctx, H->thr, R.nrounds);
+    rl0::fill_tables(A->m, A->d, k, R, &H->ctx, H->thr, R.nrounds);
     H->ctx.y = y_dev;
     H->ctx.x = xhat_dev;
     H->ctx.want_log = 0;

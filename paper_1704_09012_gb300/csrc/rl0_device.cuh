@@ -1,0 +1,229 @@
+// rl0_device.cuh -- device building blocks shared by the single-instance round
+// kernels and the batched decoder, so both run the same arithmetic in the same
+// order (Robust-l0, arXiv 1704.09012, Algorithm 2).
+#pragma once
+
+#include "rl0_common.cuh"
+
+// ---------------------------------------------------------------------------
+// Posterior evaluation in FP32: 1/p_breve(w) = sum_q a_q exp(b_q w^2)
+// (Eqs. (pz_approx)/(pe_approx) normalised per Eq. (breve)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float series_eval(const Series &S, float w)
+{
+    if (w == 0.0f) return 1.0f;                 // p_breve(0) = 1 exactly
+    if (fabsf(w) > S.cut) return 0.0f;          // below 2^-40
+    const float u = w * w;
+    float acc;
+    if (S.use_poly) {
+        const float t = fmaf(u, S.inv_u2, -1.0f);
+        const float t2 = 2.0f * t;
+        float b1 = 0.0f, b2 = 0.0f;
+        for (int k = S.npoly - 1; k >= 1; --k) {   // Clenshaw recurrence
+            const float b0 = fmaf(t2, b1, S.poly[k] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+        const float G = fmaf(t, b1, S.poly[0] - b2);
+        acc = fmaf(expf(S.b1 * u), G, S.a[0]);
+    } else {
+        acc = S.a[0];
+        for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * u);
+    }
+    return 1.0f / acc;
+}
+
+// Fixed-shape FP64 tree over `n` consecutive threads starting at `base`
+// (n a power of two): sh[t] += sh[t + off] for off = n/2 .. 1.  Every thread
+// of the block must call it (it synchronises the block).
+__device__ __forceinline__ double group_sum_f64(double v, double *sh, int lane, int n)
+{
+    sh[lane] = v;
+    __syncthreads();
+    for (int off = n >> 1; off > 0; off >>= 1) {
+        if (lane < off) sh[lane] += sh[lane + off];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_sum_f64(double v, double *sh)
+{
+    return group_sum_f64(v, sh, threadIdx.x, blockDim.x);
+}
+
+// Chunk partials combined in a fixed order by one warp: lane l sums chunks
+// l, l+32, ... then an xor-butterfly.  Call with all 32 lanes of one warp.
+__device__ __forceinline__ double warp_sum_parts(const double *parts, int nparts, int lane)
+{
+    double v = 0.0;
+    for (int c = lane; c < nparts; c += 32) v += parts[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Sort 8 column ids ascending (Batcher's 19-comparator network).
+#define RL0_CSWAP(i, j) { const int lo_ = min(js[i], js[j]), hi_ = max(js[i], js[j]); js[i] = lo_; js[j] = hi_; }
+__device__ __forceinline__ void sort8(int *js)
+{
+    RL0_CSWAP(0, 1) RL0_CSWAP(2, 3) RL0_CSWAP(4, 5) RL0_CSWAP(6, 7)
+    RL0_CSWAP(0, 2) RL0_CSWAP(1, 3) RL0_CSWAP(4, 6) RL0_CSWAP(5, 7)
+    RL0_CSWAP(1, 2) RL0_CSWAP(5, 6) RL0_CSWAP(0, 4) RL0_CSWAP(1, 5)
+    RL0_CSWAP(2, 6) RL0_CSWAP(3, 7) RL0_CSWAP(2, 4) RL0_CSWAP(3, 5)
+    RL0_CSWAP(1, 2) RL0_CSWAP(3, 4) RL0_CSWAP(5, 6)
+}
+#undef RL0_CSWAP
+
+// Exact score of one anchor s of one column (Alg. 2's inner test):
+//   n_e = sum_l q_e(r_s - r_l), w = sum_l r_l q_e(r_s - r_l) / n_e,
+//   pass <=> sum_l |r_l - w| <= sum_l |r_l|  and  n_e - n_z >= alpha.
+// The column's residuals are rc[l * stride], l < d, in slot order.
+template <bool IND>
+__device__ __forceinline__ bool score_anchor(const float *rc, int stride, int d, int s, float te,
+                                             const Series &pe, float nz, float rhs, float alpha,
+                                             float *score_out, float *w_out)
+{
+    const float rs = rc[s * stride];
+    float ne = 0.0f, num = 0.0f;
+#pragma unroll 1
+    for (int l = 0; l < d; ++l) {
+        const float rl = rc[l * stride];
+        const float q = IND ? (fabsf(rs - rl) <= te ? 1.0f : 0.0f) : series_eval(pe, rs - rl);
+        ne += q;
+        num += rl * q;
+    }
+    const float w = num / ne;
+    float lhs = 0.0f;
+#pragma unroll 1
+    for (int l = 0; l < d; ++l) lhs += fabsf(rc[l * stride] - w);
+    const float score = ne - nz;
+    *score_out = score;
+    *w_out = w;
+    return lhs <= rhs && score >= alpha;
+}
+
+// Fast-path bound of Alg. 2's test for every anchor of a column held in
+// registers: the anchors (|r_i| >= ta) whose n_e can still reach
+// n_z + alpha, with n_e <= 1 + #{l != i : |r_i - r_l| <= reach}.
+template <int DMAX, bool IND>
+__device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, float ta, float reach, float nz,
+                                                      float alpha)
+{
+    unsigned amask = 0;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s)
+        if (s < d && fabsf(r[s]) >= ta) amask |= 1u << s;
+    if (!amask) return 0u;
+    unsigned nm[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) nm[s] = 0u;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+#pragma unroll
+        for (int l = s + 1; l < DMAX; ++l) {
+            if (l < d && fabsf(r[s] - r[l]) <= reach) {
+                nm[s] |= 1u << l;
+                nm[l] |= 1u << s;
+            }
+        }
+    }
+    const float need = IND ? alpha : alpha - 1e-3f;
+    unsigned cand = 0;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s)
+        if (((amask >> s) & 1u) && (1.0f + (float)__popc(nm[s])) - nz >= need) cand |= 1u << s;
+    return cand;
+}
+
+// ---------------------------------------------------------------------------
+// H_k (Alg. 2): keep the k entries of largest |x_j|, ties to the smaller j.
+// Radix select of the k-th largest 63-bit key (bits(|x|) << 32 | ~j) among the
+// listed nonzero entries, six passes of at most 11 bits, by one CTA of NT
+// threads; everything below the key is zeroed and logged for undo.
+// ---------------------------------------------------------------------------
+#define HK_BINS 2048
+
+__device__ __forceinline__ unsigned long long hk_key(float v, int j)
+{
+    return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (unsigned long long)(0xffffffffu - (unsigned)j);
+}
+
+struct HkShared {
+    unsigned hist[HK_BINS];
+    unsigned long long prefix;
+    unsigned need;
+};
+
+template <int NT>
+__device__ void cta_hk_select(const int *list, unsigned total, float *x, long long k, unsigned long long *keys,
+                              UndoEntry *dlog, unsigned *drop_count, HkShared &sm, unsigned *suf)
+{
+    constexpr int BPT = HK_BINS / NT;          // bins per thread
+    const int t = threadIdx.x;
+    for (unsigned e = t; e < total; e += NT) {
+        const int j = list[e];
+        const float v = x[j];
+        keys[e] = (v != 0.0f) ? hk_key(v, j) : 0ull;
+    }
+    if (t == 0) { sm.prefix = 0ull; sm.need = (unsigned)k; }
+    __syncthreads();
+    const int shifts[6] = {52, 41, 30, 19, 8, 0};
+    const int widths[6] = {11, 11, 11, 11, 11, 8};
+    for (int p = 0; p < 6; ++p) {
+        const int sh = shifts[p], wd = widths[p];
+        const int nb = 1 << wd;
+        for (int b = t; b < HK_BINS; b += NT) sm.hist[b] = 0;
+        const unsigned long long prefix = sm.prefix;
+        const unsigned need = sm.need;
+        __syncthreads();
+        for (unsigned e = t; e < total; e += NT) {
+            const unsigned long long key = keys[e];
+            if (key != 0ull && (key >> (sh + wd)) == prefix) atomicAdd(&sm.hist[(unsigned)(key >> sh) & (nb - 1)], 1u);
+        }
+        __syncthreads();
+        // thread t owns bins nb-1-BPT*t .. nb-BPT*(t+1) (highest first)
+        unsigned own = 0;
+#pragma unroll
+        for (int q = 0; q < BPT; ++q) {
+            const int b = nb - 1 - BPT * t - q;
+            if (b >= 0) own += sm.hist[b];
+        }
+        suf[t] = own;
+        __syncthreads();
+        for (int off = 1; off < NT; off <<= 1) {
+            const unsigned v = (t >= off) ? suf[t - off] : 0u;
+            __syncthreads();
+            suf[t] += v;
+            __syncthreads();
+        }
+        unsigned run = suf[t] - own;               // count in bins above this thread's bins
+#pragma unroll
+        for (int q = 0; q < BPT; ++q) {
+            const int b = nb - 1 - BPT * t - q;
+            if (b >= 0) {
+                const unsigned hb = sm.hist[b];
+                if (run < need && run + hb >= need) {
+                    sm.prefix = (prefix << wd) | (unsigned)b;
+                    sm.need = need - run;
+                }
+                run += hb;
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long kth = sm.prefix;      // the k-th largest key
+    for (unsigned e = t; e < total; e += NT) {
+        const unsigned long long key = keys[e];
+        if (key != 0ull && key < kth) {
+            const int j = list[e];
+            UndoEntry u;
+            u.j = j;
+            u.old = x[j];
+            x[j] = 0.0f;
+            dlog[atomicAdd(drop_count, 1u)] = u;
+        }
+    }
+    __syncthreads();
+}
