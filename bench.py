@@ -134,6 +134,59 @@ def traffic_for(kernel):
     return rec.get("dram_bytes_per_launch")
 
 
+def bench_batched(rl0, torch, count, steps, flush, plain=True):
+    """The batched workload: `count` independent instances, n uniform over [2^10, 2^16],
+    delta in [0.1, 0.3], rho in [0.05, 0.2], d = 7, SNR in [30, 60] dB, continuous scores,
+    decoded in one persistent launch; the same instances decoded one by one with
+    rl0_decode are timed beside it (equal work, bitwise-equal results)."""
+    import numpy as np
+    import gm
+    shapes = gm.batch_shapes(count, seed=0)
+    As, ys, ks, ps = [], [], [], []
+    for i, sh in enumerate(shapes):
+        A = rl0.Expander.random(sh["n"], sh["m"], sh["d"], seed=50000 + i)
+        x, _ = gm.draw_signal(sh["n"], sh["k"], 1.0, 50000 + i)
+        ys.append(rl0.sketch(A, torch.from_numpy(x).cuda(), sigma_n=sh["sigma_n"], noise_seed=90000 + i))
+        As.append(A)
+        ks.append(sh["k"])
+        ps.append(dict(sigma_n=sh["sigma_n"]))
+    outs = [torch.empty(A.n, dtype=torch.float32, device="cuda") for A in As]
+    stream = torch.cuda.current_stream()
+    rl0.decode_batched(As, ys, ks, ps, outs=outs)                 # warm-up (and schedule tuning)
+    times, stats = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, stats = rl0.decode_batched(As, ys, ks, ps, outs=outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    nnz_rounds = sum(A.n * A.d * st["rounds"] for A, st in zip(As, stats))
+    ms = sum(times) / len(times)
+    res = {"workload": "%d instances, n~U[2^10,2^16], delta~U[0.1,0.3], rho~U[0.05,0.2], d=7, SNR~U[30,60] dB, "
+                       "continuous scores, one persistent launch" % count,
+           "ms_per_batch": ms, "value": nnz_rounds / (ms * 1e-3), "unit": UNIT,
+           "total_nnz": int(sum(A.n * A.d for A in As)), "rounds_mean": float(np.mean([s["rounds"] for s in stats])),
+           "converged_frac": float(np.mean([s["converged"] for s in stats]))}
+    if plain:
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for A, y, k, p, o in zip(As, ys, ks, ps, outs):
+            rl0.decode(A, y, k, out=o, **p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pm = e0.elapsed_time(e1)
+        res["plain_loop_ms"] = pm
+        res["plain_loop_value"] = nnz_rounds / (pm * 1e-3)
+        res["speedup_vs_plain_loop"] = pm / ms
+    for A in As:
+        A.free()
+    return res
+
+
 def cpu_baseline(cfg, seed, budget_s=20.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample: full-size rounds
     from the start of the decode (x_hat = 0) until the time budget is spent."""
@@ -209,6 +262,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quantised", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=4096, help="instances of the batched sub-measurement (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -332,6 +386,8 @@ def main():
         "clocks": clk.summary(),
         "wall_s": t_wall,
     }
+    if args.batched > 0:
+        line["batched"] = bench_batched(rl0, torch, args.batched, max(1, min(args.steps, 3)), flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, seed)
     if rank == 0:
