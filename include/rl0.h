@@ -86,6 +86,8 @@ typedef struct {
     float   ms_rebuild;        /* scatter + residual rebuild                                 */
     float   ms_accept;         /* accept / undo                                              */
     int     launches;          /* kernels launched by the decode                             */
+    int     analytic_rounds;   /* scorer = 1: rounds of the analytic continuation (0 if the  */
+                               /* learned decode converged on its own)                       */
 } rl0_stats;
 
 /* Def. "Generating model", item 1: draw A with each column's support uniform
@@ -195,6 +197,55 @@ typedef struct {
 } rl0_round_record;
 
 int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap);
+
+/* ---- Learned column scorer (an addition to the paper's method) ------------------------
+ * A 16 -> 32 -> 32 -> 1 MLP with ReLU hidden layers whose logit replaces Algorithm 2's
+ * consensus test n_e - n_z >= alpha when rl0_params.scorer = 1: an anchor passes when
+ * the l1 test holds, n_e - n_z >= 1.5 and logit >= log(mlp_threshold / (1 - mlp_threshold)),
+ * and the column takes its passing anchor of largest logit.  Features, in this order: the 7 smallest |r_l - w| / sigma_n
+ * (clipped at 8, padded with 8), n_e/d, n_z/d, log(1 + |w|/sigma_n)/5, the column's
+ * relative l1 gain (clipped to [-1, 1]), t, d k/m, (n_e - n_z)/d, 0, 0.  If the learned
+ * decode ends unconverged, the analytic decode continues from its x_hat.
+ * Parameters: RL0_MLP_PARAMS (= 1633) values, W1 (16x32, input-major), b1 (32),
+ * W2 (32x32), b2 (32), w3 (32), b3; FP32 for training, BF16 for decoding. */
+#define RL0_MLP_PARAMS 1633
+
+/* Features of every learned-scorer candidate of one round from an injected state
+ * (x_hat, r_hat: device, n and m floats) at t = 1 - round_index c: feat_dev
+ * (cap x 16 floats), meta_dev (cap x 4 int32: column, slot, passes the analytic test,
+ * passes the l1 test), omega_dev (cap floats: the consensus value w).  *count_out
+ * (host) receives the number of candidates (only min(count, cap) are written).
+ * Requires sigma_n > 0 and d <= 16. */
+int rl0_candidate_features(const rl0_expander *A, const float *y_dev, int64_t k,
+                           const rl0_params *params, int round_index, const float *xhat_dev,
+                           const float *rhat_dev, float *feat_dev, int32_t *meta_dev,
+                           float *omega_dev, int cap, int *count_out, void *cuda_stream);
+
+/* FP32 parameters, He-normal weights and zero biases from a counter-based hash of seed. */
+int rl0_mlp_init(uint64_t seed, float *w_dev, void *cuda_stream);
+
+/* Mean binary cross-entropy (logits vs labels in {0,1}) of N feature rows and its
+ * gradient w.r.t. the FP32 parameters; deterministic (fixed summation order).
+ * loss_host may be NULL.  Synchronises the stream. */
+int rl0_mlp_grad(const float *w_dev, const float *feat_dev, const float *label_dev, int64_t N,
+                 float *grad_dev, double *loss_host, void *cuda_stream);
+
+/* Adam on minibatches of `batch` consecutive rows, `epochs` passes, learning rate lr;
+ * updates w_dev in place, writes the BF16 copy to wbf16_dev (may be NULL) and the final
+ * full-set loss to loss_host (may be NULL).  Synchronises the stream. */
+int rl0_mlp_train(float *w_dev, const float *feat_dev, const float *label_dev, int64_t N,
+                  int epochs, int batch, float lr, void *wbf16_dev, double *loss_host,
+                  void *cuda_stream);
+
+/* BF16 copy (round to nearest even) of FP32 parameters, for rl0_params.mlp. */
+int rl0_mlp_export(const float *w_dev, void *wbf16_dev, void *cuda_stream);
+
+/* Logits of N feature rows with BF16 parameters (the decoder's arithmetic). */
+int rl0_mlp_forward(const void *wbf16_dev, const float *feat_dev, int64_t N, float *logit_dev,
+                    void *cuda_stream);
+
+/* RL0_MLP_PARAMS, for bindings. */
+int rl0_mlp_params(void);
 
 const char *rl0_strerror(int code);
 

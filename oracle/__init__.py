@@ -35,6 +35,9 @@ class Params(C.Structure):
         ("max_rounds", C.c_int),
         ("noiseless_tol", C.c_double),
         ("literal_ei_test", C.c_int),
+        ("learned", C.c_int),
+        ("mlp", C.c_void_p),
+        ("mlp_threshold", C.c_double),
     ]
 
 
@@ -50,6 +53,7 @@ class Stats(C.Structure):
         ("stop_level", C.c_double),
         ("ell", C.c_int),
         ("nrounds_max", C.c_int),
+        ("analytic_rounds", C.c_int),
     ]
 
 
@@ -98,6 +102,9 @@ def lib():
         L.orc_tail_constants.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                          C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_sizeof.argtypes = [C.c_int]
+        L.orc_mlp_logits.argtypes = [dp, i64, dp, dp]
+        L.orc_features.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, C.c_double, dp]
         assert L.orc_sizeof(0) == C.sizeof(Params)
         assert L.orc_sizeof(1) == C.sizeof(Stats)
         assert L.orc_sizeof(2) == C.sizeof(RoundLog)
@@ -171,10 +178,21 @@ def hard_threshold(x, k):
     return x
 
 
+_keep = []
+
+
 def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell=0,
-                max_rounds=0, noiseless_tol=0.0, literal_ei_test=False):
+                max_rounds=0, noiseless_tol=0.0, literal_ei_test=False, mlp_bf16=None, mlp_threshold=0.0):
+    """mlp_bf16: the learned scorer's parameters as a uint16 array of BF16 bit patterns
+    (enables the learned rule); None keeps Algorithm 2's analytic rule."""
+    ptr = None
+    if mlp_bf16 is not None:
+        arr = np.ascontiguousarray(mlp_bf16, dtype=np.uint16)
+        _keep.append(arr)
+        del _keep[:-8]
+        ptr = arr.ctypes.data
     return Params(sigma_s, sigma_n, int(quantised), 0, c, alpha, ell, max_rounds,
-                  noiseless_tol, int(literal_ei_test))
+                  noiseless_tol, int(literal_ei_test), int(mlp_bf16 is not None), ptr, mlp_threshold)
 
 
 def decode(rows, yhat, k, log_cap=256, **kw):
@@ -251,3 +269,25 @@ def tail_constants(which, d, rho, sigma_s, sigma_n, ell):
     _check(lib().orc_tail_constants(0 if which == "z" else 1, d, rho, sigma_s, sigma_n, ell,
                                     C.byref(R), C.byref(v)))
     return R.value, v.value
+
+
+def mlp_logits(W, F):
+    """Logits of the learned scorer's network (FP64) for rows F (n x 16)."""
+    W = _f64(W)
+    F = _f64(np.atleast_2d(F))
+    out = np.zeros(F.shape[0])
+    lib().orc_mlp_logits(W, F.shape[0], F, out)
+    return out
+
+
+def features(rl, w, ne, nz, lhs, rhs, sigma_n, t, drho):
+    """The learned scorer's 16 features of one candidate (FP64)."""
+    rl = _f64(rl)
+    f = np.zeros(16)
+    lib().orc_features(rl.size, rl, w, ne, nz, lhs, rhs, sigma_n, t, drho, f)
+    return f
+
+
+def bf16_to_f64(bits):
+    """BF16 bit patterns (uint16) -> float64, exactly."""
+    return (np.asarray(bits, np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)

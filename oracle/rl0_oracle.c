@@ -311,6 +311,9 @@ typedef struct {
     int max_rounds;       /* 0 = all rounds with t > 0                       */
     double noiseless_tol; /* 0 = 1e-5 (equality tolerance when sigma_n = 0)  */
     int literal_ei_test;  /* 1: the printed |r_i - w| <= |r_i| test          */
+    int learned;          /* 1: the learned column scorer replaces n_e - n_z >= alpha */
+    const uint16_t *mlp;  /* its parameters as BF16 bit patterns (1633 values)   */
+    double mlp_threshold; /* accept when sigmoid(logit) >= this; 0 = 0.5        */
 } orc_params;
 
 typedef struct {
@@ -321,6 +324,7 @@ typedef struct {
     double final_l1;       /* ||r_hat||_1 at exit                            */
     double c, alpha, stop_level;
     int ell, nrounds_max;
+    int analytic_rounds;   /* learned decodes: rounds of the analytic continuation */
 } orc_stats;
 
 typedef struct {
@@ -332,8 +336,77 @@ typedef struct {
     int64_t support;       /* |supp x'| after H_k                            */
 } orc_round_log;
 
+/* ---- Learned column scorer (not in the paper: an addition whose
+ * definition is fixed by the CUDA library's header) -------------------------
+ * Features of a candidate, in order: the 7 smallest |r_l - w| / sigma_n
+ * (clipped at 8, padded with 8), n_e/d, n_z/d, log(1 + |w|/sigma_n)/5, the
+ * relative l1 gain (sum|r_l| - sum|r_l - w|) / sum|r_l| clipped to [-1, 1],
+ * t, d k/m, (n_e - n_z)/d, 0, 0.  Network: 16 -> 32 -> 32 -> 1, ReLU hidden
+ * layers, parameters W1 (16x32, input-major), b1, W2 (32x32), b2, w3, b3.    */
+#define ORC_NFEAT 16
+#define ORC_HID 32
+#define ORC_MLP_PARAMS (ORC_NFEAT * ORC_HID + ORC_HID + ORC_HID * ORC_HID + ORC_HID + ORC_HID + 1)
+
+double orc_bf16_to_double(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
+void orc_features(int d, const double *rl, double w, double ne, double nz, double lhs, double rhs,
+                  double sigma_n, double t, double drho, double *f)
+{
+    double dev[64];
+    int used[64];
+    for (int l = 0; l < d; ++l) {
+        double v = fabs(rl[l] - w) / sigma_n;
+        dev[l] = v < 8.0 ? v : 8.0;
+        used[l] = 0;
+    }
+    for (int q = 0; q < 7; ++q) {          /* the 7 smallest, padded with 8 */
+        double best = 8.0;
+        int bi = -1;
+        for (int l = 0; l < d; ++l)
+            if (!used[l] && dev[l] < best) { best = dev[l]; bi = l; }
+        if (bi >= 0) used[bi] = 1;
+        f[q] = best;
+    }
+    f[7] = ne / d;
+    f[8] = nz / d;
+    f[9] = log1p(fabs(w) / sigma_n) / 5.0;
+    double g = (rhs - lhs) / (rhs > 1e-30 ? rhs : 1e-30);
+    f[10] = g < -1.0 ? -1.0 : (g > 1.0 ? 1.0 : g);
+    f[11] = t;
+    f[12] = drho;
+    f[13] = (ne - nz) / d;
+    f[14] = 0.0;
+    f[15] = 0.0;
+}
+
+double orc_mlp_logit(const double *W, const double *f)
+{
+    const double *W1 = W, *b1 = W1 + ORC_NFEAT * ORC_HID, *W2 = b1 + ORC_HID, *b2 = W2 + ORC_HID * ORC_HID;
+    const double *w3 = b2 + ORC_HID, *b3 = w3 + ORC_HID;
+    double h1[ORC_HID], out = b3[0];
+    for (int o = 0; o < ORC_HID; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < ORC_NFEAT; ++i) a += f[i] * W1[i * ORC_HID + o];
+        h1[o] = a > 0.0 ? a : 0.0;
+    }
+    for (int o = 0; o < ORC_HID; ++o) {
+        double a = b2[o];
+        for (int i = 0; i < ORC_HID; ++i) a += h1[i] * W2[i * ORC_HID + o];
+        out += (a > 0.0 ? a : 0.0) * w3[o];
+    }
+    return out;
+}
+
 typedef struct {
     orc_series pz, pe;
+    double drho;                     /* d k / m, a feature of the learned scorer */
+    double mlp[ORC_MLP_PARAMS];      /* its parameters, decoded from BF16        */
 } orc_post;
 
 /* Eq. (finetune_c_quant) and Eq. (finetune_c_cont).                         */
@@ -372,6 +445,11 @@ static void orc_resolve(const orc_params *in, int d, int64_t n, int64_t m, int64
 static int orc_post_init(orc_post *P, int d, double rho, const orc_params *p)
 {
     double s2 = p->sigma_s * p->sigma_s, n2 = p->sigma_n * p->sigma_n;
+    P->drho = d * rho;
+    if (p->learned) {
+        if (!p->mlp || !(p->sigma_n > 0.0)) return ORC_EINVAL;
+        for (int q = 0; q < ORC_MLP_PARAMS; ++q) P->mlp[q] = orc_bf16_to_double(p->mlp[q]);
+    }
     int rc = orc_series_init(&P->pz, d * rho, s2, n2, p->ell, 0, p->noiseless_tol);
     if (rc) return rc;
     return orc_series_init(&P->pe, 2.0 * d * rho, s2, 2.0 * n2, p->ell, 0, p->noiseless_tol);
@@ -518,7 +596,22 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                 slack = fabs(m1 < m2 ? m1 : m2);
             }
             if (slack < margin) margin = slack;
-            if (lhs <= rhs && score >= p->alpha) {
+            if (p->learned) {
+                /* learned rule: l1 test, n_e - n_z >= 1.5, logit >= logit(threshold);
+                 * the column takes its passing anchor of largest logit */
+                if (lhs <= rhs && score >= 1.5) {
+                    double f[ORC_NFEAT];
+                    orc_features(d, rl, w, ne, nz, lhs, rhs, p->sigma_n, t, P->drho, f);
+                    double lg = orc_mlp_logit(P->mlp, f);
+                    double th = p->mlp_threshold > 0.0 ? p->mlp_threshold : 0.5;
+                    double lt = log(th / (1.0 - th));
+                    double ml = fabs(lg - lt);
+                    if (ml < margin) margin = ml;
+                    double m3 = fabs(score - 1.5);
+                    if (m3 < margin) margin = m3;
+                    if (lg >= lt && (best < 0 || lg > best_score)) { best = s; best_score = lg; best_w = w; }
+                }
+            } else if (lhs <= rhs && score >= p->alpha) {
                 if (best < 0 || score > best_score) { best = s; best_score = score; best_w = w; }
             }
         }
@@ -561,16 +654,17 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
     if (pin->adaptive_k) return ORC_EINVAL;
     orc_params p;
     orc_resolve(pin, d, n, m, k, &p);
-    orc_post P;
-    int rc = orc_post_init(&P, d, (double)k / (double)m, &p);
-    if (rc) return rc;
+    orc_post *PP = (orc_post *)malloc(sizeof(orc_post));
+    if (!PP) return ORC_ENOMEM;
+    int rc = orc_post_init(PP, d, (double)k / (double)m, &p);
+    if (rc) { free(PP); return rc; }
     int R = orc_num_rounds(p.c);
     if (p.max_rounds > 0 && p.max_rounds < R) R = p.max_rounds;
 
     double *rh = (double *)malloc((size_t)m * sizeof(double));
     double *xp = (double *)malloc((size_t)n * sizeof(double));
     double *rp = (double *)malloc((size_t)m * sizeof(double));
-    if (!rh || !xp || !rp) { free(rh); free(xp); free(rp); return ORC_ENOMEM; }
+    if (!rh || !xp || !rp) { free(rh); free(xp); free(rp); free(PP); return ORC_ENOMEM; }
 
     for (int64_t j = 0; j < n; ++j) xhat[j] = 0.0;        /* x_hat <- 0 */
     for (int64_t i = 0; i < m; ++i) rh[i] = yhat[i];      /* r_hat <- y */
@@ -581,7 +675,7 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
         if (l1h <= stop) break;                           /* converged */
         double t = 1.0 - r * p.c;
         int64_t upd = 0;
-        rc = orc_round_step(n, m, d, rows, yhat, k, &P, &p, t, xhat, rh, xp, rp, &upd, NULL);
+        rc = orc_round_step(n, m, d, rows, yhat, k, PP, &p, t, xhat, rh, xp, rp, &upd, NULL);
         if (rc) break;
         double l1 = l1norm(m, rp);
         int accepted = (l1 < l1h);                        /* strict, as printed */
@@ -603,10 +697,37 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
         }
         rounds++;
     }
+    int analytic_rounds = 0;
+    if (!rc && p.learned && !(l1h <= stop)) {
+        /* not converged with the learned scorer: the analytic rule continues
+         * from x_hat with a fresh sweep from t = 1 */
+        orc_params p2 = p;
+        p2.learned = 0;
+        orc_matvec(n, m, d, rows, xhat, rh);
+        for (int64_t i = 0; i < m; ++i) rh[i] = yhat[i] - rh[i];
+        l1h = l1norm(m, rh);
+        for (int r = 0; r < R; ++r) {
+            if (l1h <= stop) break;
+            double t = 1.0 - r * p2.c;
+            int64_t upd = 0;
+            rc = orc_round_step(n, m, d, rows, yhat, k, PP, &p2, t, xhat, rh, xp, rp, &upd, NULL);
+            if (rc) break;
+            double l1 = l1norm(m, rp);
+            if (l1 < l1h) {
+                memcpy(xhat, xp, (size_t)n * sizeof(double));
+                memcpy(rh, rp, (size_t)m * sizeof(double));
+                l1h = l1;
+                acc_rounds++;
+            }
+            rounds++;
+            analytic_rounds++;
+        }
+    }
     if (st) {
         int64_t supp = 0;
         for (int64_t j = 0; j < n; ++j) supp += (xhat[j] != 0.0);
         st->rounds = rounds;
+        st->analytic_rounds = analytic_rounds;
         st->accepted_rounds = acc_rounds;
         st->converged = (l1h <= stop);
         st->support_size = supp;
@@ -614,7 +735,7 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
         st->c = p.c; st->alpha = p.alpha; st->stop_level = stop;
         st->ell = p.ell; st->nrounds_max = R;
     }
-    free(rh); free(xp); free(rp);
+    free(rh); free(xp); free(rp); free(PP);
     return rc;
 }
 
@@ -626,11 +747,14 @@ int orc_round(int64_t n, int64_t m, int d, const int32_t *rows, const double *yh
 {
     orc_params p;
     orc_resolve(pin, d, n, m, k, &p);
-    orc_post P;
-    int rc = orc_post_init(&P, d, (double)k / (double)m, &p);
-    if (rc) return rc;
+    orc_post *P = (orc_post *)malloc(sizeof(orc_post));
+    if (!P) return ORC_ENOMEM;
+    int rc = orc_post_init(P, d, (double)k / (double)m, &p);
+    if (rc) { free(P); return rc; }
     double t = 1.0 - round_index * p.c;
-    return orc_round_step(n, m, d, rows, yhat, k, &P, &p, t, xh, rh, xp, rp, updated, rec);
+    rc = orc_round_step(n, m, d, rows, yhat, k, P, &p, t, xh, rh, xp, rp, updated, rec);
+    free(P);
+    return rc;
 }
 
 /* Alg. 1 (Parallel-l0), noiseless.  Equality and zero tests use the absolute
@@ -725,4 +849,11 @@ int orc_sizeof(int which)
     case 3: return (int)sizeof(orc_col_rec);
     default: return -1;
     }
+}
+
+/* Learned-scorer pieces exposed for pins: features of one candidate and the
+ * network's logit for FP64 parameters (n rows of 16 features).            */
+void orc_mlp_logits(const double *W, int64_t nrows, const double *F, double *out)
+{
+    for (int64_t s = 0; s < nrows; ++s) out[s] = orc_mlp_logit(W, F + s * ORC_NFEAT);
 }

@@ -31,7 +31,11 @@ EXPORTS = [
     "rl0_make_expander", "rl0_expander_from_rows", "rl0_expander_rows", "rl0_expander_shape",
     "rl0_free_expander", "rl0_sketch", "rl0_decode", "rl0_decode_host", "rl0_round_step",
     "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static",
+    "rl0_candidate_features", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
+    "rl0_mlp_forward", "rl0_mlp_params",
 ]
+MLP_PARAMS = 1633
+NFEAT = 16
 
 
 class Rl0Error(RuntimeError):
@@ -55,6 +59,7 @@ class Stats(C.Structure):
         ("support_size", C.c_int64), ("final_l1", C.c_double), ("ms", C.c_float), ("hk_rounds", C.c_int),
         ("fallback_rounds", C.c_int), ("ms_score", C.c_float), ("ms_hk", C.c_float),
         ("ms_rebuild", C.c_float), ("ms_accept", C.c_float), ("launches", C.c_int),
+        ("analytic_rounds", C.c_int),
     ]
 
     def as_dict(self):
@@ -94,6 +99,15 @@ def _lib():
                                          C.POINTER(vp), vp, vp]
         L.rl0_decode_log.argtypes = [vp, C.POINTER(RoundRecord), i32]
         L.rl0_decode_static.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.POINTER(Stats), vp]
+        L.rl0_candidate_features.argtypes = [vp, vp, i64, C.POINTER(Params), i32, vp, vp, vp, vp, vp, i32,
+                                             C.POINTER(i32), vp]
+        L.rl0_mlp_init.argtypes = [C.c_uint64, vp, vp]
+        L.rl0_mlp_grad.argtypes = [vp, vp, vp, i64, vp, C.POINTER(C.c_double), vp]
+        L.rl0_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, vp, C.POINTER(C.c_double), vp]
+        L.rl0_mlp_export.argtypes = [vp, vp, vp]
+        L.rl0_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.rl0_mlp_params.argtypes = []
+        assert L.rl0_mlp_params() == MLP_PARAMS
         L.rl0_strerror.argtypes = [i32]
         L.rl0_strerror.restype = C.c_char_p
         _L = L
@@ -263,3 +277,71 @@ def decode_batched(As, ys, ks, params=None, outs=None, stream=None):
     _check(_lib().rl0_decode_batched(cnt, Ah, Yh, K, C.cast(P, C.c_void_p), Xh, C.cast(S, C.c_void_p),
                                      _stream(stream)), "rl0_decode_batched")
     return xs, [s.as_dict() for s in S]
+
+
+# ---------------------------------------------------------------------------
+# Learned column scorer (an addition to the paper's method; see include/rl0.h)
+# ---------------------------------------------------------------------------
+def candidate_features(A, y, k, round_index, xhat, rhat, cap=None, stream=None, **params):
+    """Features of every learned-scorer candidate of one round from an injected state.
+
+    Returns (features [c, 16] float32, meta [c, 4] int32 (column, slot, analytic pass,
+    l1 test), omega [c] float32), all CUDA tensors."""
+    p = make_params(**params)
+    if cap is None:
+        cap = 4 * A.n
+    feat = torch.empty((cap, NFEAT), dtype=torch.float32, device="cuda")
+    meta = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    omega = torch.empty(cap, dtype=torch.float32, device="cuda")
+    cnt = C.c_int()
+    _check(_lib().rl0_candidate_features(A.handle, _dev(y, torch.float32, A.m, "y"), int(k), C.byref(p),
+                                         int(round_index), _dev(xhat, torch.float32, A.n, "x_hat"),
+                                         _dev(rhat, torch.float32, A.m, "r_hat"), C.c_void_p(feat.data_ptr()),
+                                         C.c_void_p(meta.data_ptr()), C.c_void_p(omega.data_ptr()), int(cap),
+                                         C.byref(cnt), _stream(stream)), "rl0_candidate_features")
+    c = min(cnt.value, cap)
+    return feat[:c], meta[:c], omega[:c]
+
+
+def mlp_init(seed=0, stream=None):
+    w = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    _check(_lib().rl0_mlp_init(int(seed), C.c_void_p(w.data_ptr()), _stream(stream)), "rl0_mlp_init")
+    return w
+
+
+def mlp_grad(w, feat, label, stream=None):
+    """(mean BCE loss, gradient) of the FP32 parameters on rows feat [N, 16], labels [N]."""
+    N = feat.shape[0]
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = C.c_double()
+    _check(_lib().rl0_mlp_grad(_dev(w, torch.float32, MLP_PARAMS, "w"), _dev(feat, torch.float32, N * NFEAT, "feat"),
+                               _dev(label, torch.float32, N, "label"), N, C.c_void_p(g.data_ptr()), C.byref(loss),
+                               _stream(stream)), "rl0_mlp_grad")
+    return loss.value, g
+
+
+def mlp_train(w, feat, label, epochs=5, batch=4096, lr=3e-3, stream=None):
+    """Adam on minibatches of consecutive rows (shuffle beforehand).  Trains w in place;
+    returns (BF16 parameters as a CUDA int16 tensor of bit patterns, final loss)."""
+    N = feat.shape[0]
+    wb = torch.empty(MLP_PARAMS, dtype=torch.int16, device="cuda")
+    loss = C.c_double()
+    _check(_lib().rl0_mlp_train(_dev(w, torch.float32, MLP_PARAMS, "w"), _dev(feat, torch.float32, N * NFEAT, "feat"),
+                                _dev(label, torch.float32, N, "label"), N, int(epochs), int(batch), float(lr),
+                                C.c_void_p(wb.data_ptr()), C.byref(loss), _stream(stream)), "rl0_mlp_train")
+    return wb, loss.value
+
+
+def mlp_export(w, stream=None):
+    wb = torch.empty(MLP_PARAMS, dtype=torch.int16, device="cuda")
+    _check(_lib().rl0_mlp_export(_dev(w, torch.float32, MLP_PARAMS, "w"), C.c_void_p(wb.data_ptr()),
+                                 _stream(stream)), "rl0_mlp_export")
+    return wb
+
+
+def mlp_forward(wb, feat, stream=None):
+    N = feat.shape[0]
+    out = torch.empty(N, dtype=torch.float32, device="cuda")
+    _check(_lib().rl0_mlp_forward(C.c_void_p(wb.data_ptr()), _dev(feat, torch.float32, N * NFEAT, "feat"), N,
+                                  C.c_void_p(out.data_ptr()), _stream(stream)), "rl0_mlp_forward")
+    return out

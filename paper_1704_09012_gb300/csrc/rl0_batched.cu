@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                         rhs += fabsf(v.x);
                     }
                 }
-                unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, nz, alpha)
+                unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, nz, IND ? alpha : alpha - 1e-3f)
                                        : 0u;
                 if (cand) {
 #pragma unroll

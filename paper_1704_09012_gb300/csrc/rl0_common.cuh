@@ -95,8 +95,12 @@ struct DecodeCtx {
     double stop_rel;          // > 0: stop level = stop_rel * ||y_hat||_1 (noiseless)
     Series pz, pe;
     int scorer;               // 0 analytic, 1 learned
-    const void *mlp;
+    const void *mlp;          // BF16 parameters of the learned scorer
     float mlp_threshold;
+    float logit_thr;          // learned: accept when the logit >= log(thr / (1 - thr))
+    float learned_need;       // learned: candidates need n_e - n_z bound >= this
+    float inv_sn;             // 1 / sigma_n (0 when noiseless)
+    float drho;               // d k / m
     int32_t *passed;          // optional per-column pass flags (round_step)
     int want_log;
 };

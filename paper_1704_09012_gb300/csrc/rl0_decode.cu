@@ -27,6 +27,7 @@
 
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
+#include <cuda_bf16.h>
 
 #define CK(call)                                          \
     do {                                                  \
@@ -149,11 +150,16 @@ __global__ void k_list_count_from_support(KArgs a)
 // Threads per CTA of the column kernel (its shared arrays scale with DMAX).
 template <int DMAX> struct ColBlock { static constexpr int value = DMAX <= 8 ? 256 : (DMAX <= 16 ? 128 : 64); };
 
-template <int DMAX, bool IND>
+template <int DMAX, bool IND, bool LEARNED>
 __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
 {
     constexpr int NT = ColBlock<DMAX>::value;
     __shared__ Series s_pe;
+    __shared__ float s_W[LEARNED ? RL0_MLP_PARAMS : 1];   // learned scorer parameters (FP32 copies)
+    __shared__ float s_f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the queued candidates
+    __shared__ float s_h1[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];     // hidden layers of a 32-candidate slice
+    __shared__ float s_h2[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];
+    __shared__ unsigned char s_l1ok[LEARNED ? NT : 1];
     __shared__ float s_r[DMAX][NT];           // residuals of columns with candidates
     __shared__ float s_nz[NT], s_rhs[NT];
     __shared__ unsigned short s_q[NT];        // this pass's queue: (column lane << 5) | slot
@@ -171,6 +177,10 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     if (tid == 0) {
         s_nq = 0;
         if (!IND) s_pe = ctx->pe;
+    }
+    if (LEARNED) {
+        const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
+        for (int p = tid; p < RL0_MLP_PARAMS; p += NT) s_W[p] = __bfloat162float(wb[p]);
     }
     __syncthreads();
     const int n = a.n, d = a.d;
@@ -190,7 +200,8 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             rhs += fabsf(v.x);
         }
     }
-    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, alpha) : 0u;
+    const float need = LEARNED ? (IND ? ctx->learned_need : ctx->learned_need - 1e-3f) : (IND ? alpha : alpha - 1e-3f);
+    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, need) : 0u;
     if (cand) {
 #pragma unroll
         for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
@@ -211,13 +222,60 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         }
         __syncthreads();
         const int nq = s_nq;
-        for (int e = tid; e < nq; e += NT) {
-            const int owner = s_q[e] >> 5, s = s_q[e] & 31;
-            float sc, w;
-            s_ok[e] = score_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe, s_nz[owner], s_rhs[owner], alpha,
-                                        &sc, &w) ? 1 : 0;
-            s_score[e] = sc;
-            s_w[e] = w;
+        if (LEARNED) {
+            // the learned scorer's logit replaces n_e - n_z >= alpha: features of
+            // every queued candidate, then the MLP over 32-candidate slices with
+            // one thread per (candidate, hidden unit); the FMA chains are those
+            // of mlp_logit, so the logits equal rl0_mlp_forward's
+            for (int e = tid; e < nq; e += NT) {
+                const int owner = s_q[e] >> 5, s = s_q[e] & 31;
+                const AnchorEval E = eval_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe);
+                float f[RL0_NFEAT];
+                candidate_features(&s_r[0][owner], NT, d, E, s_nz[owner], s_rhs[owner], ctx->inv_sn, th.t,
+                                   ctx->drho, f);
+#pragma unroll
+                for (int q = 0; q < RL0_NFEAT; ++q) s_f[q][e] = f[q];
+                s_l1ok[e] = (E.lhs <= s_rhs[owner] && E.ne - s_nz[owner] >= ctx->learned_need) ? 1 : 0;
+                s_w[e] = E.w;
+            }
+            __syncthreads();
+            for (int e0 = 0; e0 < nq; e0 += 32) {
+                for (int it = tid; it < 32 * RL0_HID; it += NT) {
+                    const int el = it % 32, o = it / 32, e = e0 + el;
+                    float acc = s_W[RL0_OFF_B1 + o];
+                    if (e < nq) {
+#pragma unroll
+                        for (int i = 0; i < RL0_NFEAT; ++i) acc = fmaf(s_f[i][e], s_W[RL0_OFF_W1 + i * RL0_HID + o], acc);
+                    }
+                    s_h1[o][el] = fmaxf(acc, 0.0f);
+                }
+                __syncthreads();
+                for (int it = tid; it < 32 * RL0_HID; it += NT) {
+                    const int el = it % 32, o = it / 32;
+                    float acc = s_W[RL0_OFF_B2 + o];
+#pragma unroll 8
+                    for (int i = 0; i < RL0_HID; ++i) acc = fmaf(s_h1[i][el], s_W[RL0_OFF_W2 + i * RL0_HID + o], acc);
+                    s_h2[o][el] = fmaxf(acc, 0.0f);
+                }
+                __syncthreads();
+                if (tid < 32 && e0 + tid < nq) {
+                    const int e = e0 + tid;
+                    float out = s_W[RL0_OFF_B3];
+                    for (int o = 0; o < RL0_HID; ++o) out = fmaf(s_h2[o][tid], s_W[RL0_OFF_W3 + o], out);
+                    s_score[e] = out;
+                    s_ok[e] = (s_l1ok[e] && out >= ctx->logit_thr) ? 1 : 0;
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int e = tid; e < nq; e += NT) {
+                const int owner = s_q[e] >> 5, s = s_q[e] & 31;
+                float sc, w;
+                s_ok[e] = score_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe, s_nz[owner], s_rhs[owner], alpha,
+                                            &sc, &w) ? 1 : 0;
+                s_score[e] = sc;
+                s_w[e] = w;
+            }
         }
         __syncthreads();
         if (my >= 0 && s_ok[my] && (best < 0 || s_score[my] > bscore)) {
@@ -476,6 +534,81 @@ __global__ void k_final_sum(KArgs a)
     if (threadIdx.x == 0) a.st->final_l1 = v;
 }
 
+// r_hat = y - A x_hat for an arbitrary x_hat (CSR rows, ascending columns: the
+// same FP32 sum as the rebuild) into rz[0], with the chunk l1 partials.
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
+{
+    __shared__ double sh[RL0_ROWS_CHUNK];
+    const DecodeCtx *ctx = a.ctx;
+    const float *x = ctx->x;
+    double l1 = 0.0;
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    if (i < a.m) {
+        float sum = 0.0f;
+        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
+        const float r = ctx->y[i] - sum;
+        if (!isfinite(ctx->y[i])) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
+        a.rz0[i] = make_float2(r, ctx->indicator ? 0.0f : series_eval(ctx->pz, r));
+        l1 = fabs((double)r);
+    }
+    const double s = block_sum_f64(l1, sh);
+    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+}
+
+// Features of every learned-scorer candidate of one round (for training logs):
+// feat[e*16..], meta[e*4..] = (column, slot, analytic pass, l1 test), omega[e].
+template <int DMAX, bool IND>
+__global__ void __launch_bounds__(ColBlock<DMAX>::value) k_collect(KArgs a, float *feat, int *meta, float *omega,
+                                                                   int cap, int *count)
+{
+    constexpr int NT = ColBlock<DMAX>::value;
+    __shared__ Series s_pe;
+    __shared__ float s_r[DMAX][NT];
+    const DecodeState *st = a.st;
+    const DecodeCtx *ctx = a.ctx;
+    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
+    const RoundThr th = a.thr[st->round];
+    const float alpha = ctx->alpha;
+    const int tid = threadIdx.x;
+    if (tid == 0 && !IND) s_pe = ctx->pe;
+    __syncthreads();
+    const int n = a.n, d = a.d;
+    const int j = blockIdx.x * NT + tid;
+    if (j >= n) return;
+    float r[DMAX];
+    float nz = 0.0f, rhs = 0.0f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        r[s] = 0.0f;
+        if (s < d) {
+            const float2 v = rz[a.rows_sm[(size_t)s * n + j]];
+            r[s] = v.x;
+            nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
+            rhs += fabsf(v.x);
+        }
+    }
+    const float need = IND ? ctx->learned_need : ctx->learned_need - 1e-3f;
+    unsigned cand = anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, need);
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
+    for (; cand; cand &= cand - 1u) {
+        const int s = __ffs(cand) - 1;
+        const AnchorEval E = eval_anchor<IND>(&s_r[0][tid], NT, d, s, th.te, s_pe);
+        if (!(E.ne - nz >= ctx->learned_need)) continue;
+        float f[RL0_NFEAT];
+        candidate_features(&s_r[0][tid], NT, d, E, nz, rhs, ctx->inv_sn, th.t, ctx->drho, f);
+        const int e = atomicAdd(count, 1);
+        if (e >= cap) continue;
+#pragma unroll
+        for (int q = 0; q < RL0_NFEAT; ++q) feat[(long long)e * RL0_NFEAT + q] = f[q];
+        meta[4 * e + 0] = j;
+        meta[4 * e + 1] = s;
+        meta[4 * e + 2] = (E.lhs <= rhs && E.ne - nz >= alpha) ? 1 : 0;
+        meta[4 * e + 3] = (E.lhs <= rhs) ? 1 : 0;
+        omega[e] = E.w;
+    }
+}
+
 // round_step output: the candidate residual (or r_hat when nothing changed).
 __global__ void k_extract_r(KArgs a, float *rp, int use_candidate_always)
 {
@@ -493,7 +626,7 @@ using rl0::Resolved;
 namespace {
 
 struct GraphEntry {
-    int nrounds, dmax, indicator, profile;
+    int nrounds, dmax, indicator, profile, learned;
     cudaGraphExec_t exec;
     std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
@@ -539,21 +672,24 @@ KArgs make_args(const rl0_expander *A)
     return a;
 }
 
-void launch_column_score(const KArgs &a, int dmax, int indicator, cudaStream_t s)
+void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-#define RL0_CS(D, I) k_column_score<D, I><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
-    if (dmax == 8) { if (indicator) RL0_CS(8, true); else RL0_CS(8, false); }
-    else if (dmax == 16) { if (indicator) RL0_CS(16, true); else RL0_CS(16, false); }
-    else { if (indicator) RL0_CS(32, true); else RL0_CS(32, false); }
+#define RL0_CS(D, I, L) k_column_score<D, I, L><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
+    if (learned) {
+        if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }
+        else { if (indicator) RL0_CS(16, true, true); else RL0_CS(16, false, true); }
+    } else if (dmax == 8) { if (indicator) RL0_CS(8, true, false); else RL0_CS(8, false, false); }
+    else if (dmax == 16) { if (indicator) RL0_CS(16, true, false); else RL0_CS(16, false, false); }
+    else { if (indicator) RL0_CS(32, true, false); else RL0_CS(32, false, false); }
 #undef RL0_CS
 }
 
 int dmax_of(int d) { return d <= 8 ? 8 : (d <= 16 ? 16 : 32); }
 
 // The kernels of one round (shared by the graph and by round_step).
-void launch_round(const KArgs &a, int dmax, int indicator, cudaStream_t s)
+void launch_round(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-    launch_column_score(a, dmax, indicator, s);
+    launch_column_score(a, dmax, indicator, learned, s);
     k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
     k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
     k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
@@ -580,7 +716,8 @@ int add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t 
     return RL0_OK;
 }
 
-int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int profile, GraphEntry *E)
+int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int profile, int learned,
+                         GraphEntry *E)
 {
     GraphCache *gc = (GraphCache *)A->graph_cache;
     KArgs a = make_args(A);
@@ -589,6 +726,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
     E->dmax = dmax;
     E->indicator = indicator;
     E->profile = profile;
+    E->learned = learned;
     cudaGraph_t g = nullptr;
     if (!profile) {
         CK(cudaGraphCreate(&g, 0));
@@ -620,7 +758,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
                 cudaSuccess) { rc = RL0_ERR_CUDA; break; }
-            launch_round(a, dmax, indicator, s);
+            launch_round(a, dmax, indicator, learned, s);
             k_accept<<<1, 1024, 0, s>>>(a);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
@@ -646,7 +784,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < nrounds && e == cudaSuccess; ++r) {
         e = mark(4 * r);
-        launch_column_score(a, dmax, indicator, s);
+        launch_column_score(a, dmax, indicator, learned, s);
         if (e == cudaSuccess) e = mark(4 * r + 1);
         k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
         if (e == cudaSuccess) e = mark(4 * r + 2);
@@ -800,8 +938,6 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     Resolved R;
     int rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
-    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
-    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     HostStage *H = (HostStage *)A->host_pinned;
     cached_tables(A, k, R, &H->ctx, H->thr);
     H->ctx.y = y_dev;
@@ -815,12 +951,15 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     const int dmax = dmax_of(A->d);
     GraphCache *gc = (GraphCache *)A->graph_cache;
     const int prof = R.p.profile ? 1 : 0;
+    const int learned = R.p.scorer == 1;
     GraphEntry *E = nullptr;
     for (auto &g : gc->entries)
-        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator && g.profile == prof) E = &g;
+        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator && g.profile == prof &&
+            g.learned == learned)
+            E = &g;
     if (!E) {
         GraphEntry fresh;
-        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, prof, &fresh);
+        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, prof, learned, &fresh);
         if (rc) {
             for (auto ev : fresh.events) if (ev) cudaEventDestroy(ev);
             return rc;
@@ -865,7 +1004,54 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         }
     }
     A->last_log_rounds = H->st.rounds_run;
-    return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
+    if (H->st.status) return RL0_ERR_TIMEOUT;
+    if (learned && !H->st.converged) {
+        // Not converged with the learned scorer: Algorithm 2 with the analytic
+        // scores continues from the learned x_hat (a fresh sweep from t = 1).
+        const DecodeState first = H->st;
+        Resolved R2 = R;
+        R2.p.scorer = 0;
+        R2.p.profile = 0;
+        rl0::fill_tables(A->m, A->d, k, R2, &H->ctx, H->thr, R2.nrounds);
+        H->ctx.y = y_dev;
+        H->ctx.x = xhat_dev;
+        H->ctx.want_log = 0;
+        H->ctx.passed = nullptr;
+        CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.thr, H->thr, R2.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+        const KArgs a = make_args(A);
+        k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
+        k_rows_from_x<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+        k_start<<<1, 32, 0, s>>>(a, 0, 0);
+        k_list_count_from_support<<<1, 32, 0, s>>>(a);
+        for (int r = 0; r < R2.nrounds; ++r) {
+            launch_round(a, dmax, R2.indicator, 0, s);
+            k_accept<<<1, 1024, 0, s>>>(a);
+        }
+        k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+        k_final_sum<<<1, 32, 0, s>>>(a);
+        CK(cudaGetLastError());
+        if (stats) CK(cudaEventRecord(ev[1], s));
+        CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (H->st.status) return RL0_ERR_TIMEOUT;
+        if (stats) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            stats->rounds = first.rounds_run + H->st.rounds_run;
+            stats->accepted_rounds = first.accepted_rounds + H->st.accepted_rounds;
+            stats->converged = H->st.converged;
+            stats->support_size = H->st.nnz;
+            stats->final_l1 = H->st.final_l1;
+            stats->ms = ms;
+            stats->hk_rounds = first.hk_rounds + H->st.hk_rounds;
+            stats->fallback_rounds = first.fallback_rounds + H->st.fallback_rounds;
+            stats->analytic_rounds = H->st.rounds_run;
+            stats->launches += 4 + 5 * R2.nrounds + 2;
+        }
+    }
+    return RL0_OK;
 }
 
 extern "C" int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap)
@@ -935,7 +1121,6 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     Resolved R;
     rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
-    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     if (round_index >= RL0_MAX_ROUNDS) return RL0_ERR_INVALID_ARG;
     R.nrounds = round_index + 1;
     R.stop_level = -1.0;                          // never "converged" here
@@ -956,7 +1141,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
     k_list_count_from_support<<<1, 32, 0, s>>>(a);
-    launch_round(a, dmax_of(A->d), R.indicator, s);
+    launch_round(a, dmax_of(A->d), R.indicator, R.p.scorer == 1, s);
     k_extract_r<<<2 * a.nsm, 256, 0, s>>>(a, rp_dev, 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
@@ -1058,7 +1243,6 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     Resolved R;
     rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
-    if (R.p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     unsigned char *base = nullptr;
     rc = static_scratch_base(A->device, &base);
     if (rc) return rc;
@@ -1100,7 +1284,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     for (int r = 0; r < R.nrounds; ++r) {
-        launch_round(a, dmax, R.indicator, s);
+        launch_round(a, dmax, R.indicator, R.p.scorer == 1, s);
         k_accept<<<1, 1024, 0, s>>>(a);
     }
     k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
@@ -1123,4 +1307,51 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
         stats->launches = launches_per_decode(R.nrounds);
     }
     return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
+}
+
+extern "C" int rl0_candidate_features(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
+                                      int round_index, const float *xhat_dev, const float *rhat_dev, float *feat_dev,
+                                      int32_t *meta_dev, float *omega_dev, int cap, int *count_out, void *cuda_stream)
+{
+    rl0_expander *A = const_cast<rl0_expander *>(Ac);
+    if (!A || !y_dev || !xhat_dev || !rhat_dev || !feat_dev || !meta_dev || !omega_dev || !count_out || cap < 0 ||
+        round_index < 0 || round_index >= RL0_MAX_ROUNDS)
+        return RL0_ERR_INVALID_ARG;
+    if (A->d > 16) return RL0_ERR_UNSUPPORTED;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Resolved R;
+    rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
+    if (rc) return rc;
+    if (!(R.p.sigma_n > 0.0)) return RL0_ERR_INVALID_ARG;
+    R.nrounds = round_index + 1;
+    HostStage *H = (HostStage *)A->host_pinned;
+    rl0::fill_tables(A->m, A->d, k, R, &H->ctx, H->thr, R.nrounds);
+    H->ctx.y = y_dev;
+    H->ctx.x = const_cast<float *>(xhat_dev);
+    H->ctx.want_log = 0;
+    H->ctx.passed = nullptr;
+    const Workspace &w = A->ws;
+    CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+    int *cnt = (int *)w.list_tmp;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    const KArgs a = make_args(A);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0);
+    k_start<<<1, 32, 0, s>>>(a, round_index, 0);
+    if (A->d <= 8) {
+        if (R.indicator) k_collect<8, true><<<rl0_div_up(a.n, 256), 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
+        else k_collect<8, false><<<rl0_div_up(a.n, 256), 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
+    } else {
+        if (R.indicator) k_collect<16, true><<<rl0_div_up(a.n, 128), 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
+        else k_collect<16, false><<<rl0_div_up(a.n, 128), 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
+    }
+    CK(cudaGetLastError());
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *count_out = c;
+    return RL0_OK;
 }

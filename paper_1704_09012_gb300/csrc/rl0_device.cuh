@@ -76,14 +76,16 @@ __device__ __forceinline__ void sort8(int *js)
 }
 #undef RL0_CSWAP
 
-// Exact score of one anchor s of one column (Alg. 2's inner test):
+// Exact quantities of one anchor s of one column (Alg. 2's inner test):
 //   n_e = sum_l q_e(r_s - r_l), w = sum_l r_l q_e(r_s - r_l) / n_e,
-//   pass <=> sum_l |r_l - w| <= sum_l |r_l|  and  n_e - n_z >= alpha.
+//   lhs = sum_l |r_l - w|  (compared with rhs = sum_l |r_l|).
 // The column's residuals are rc[l * stride], l < d, in slot order.
+struct AnchorEval {
+    float ne, w, lhs;
+};
+
 template <bool IND>
-__device__ __forceinline__ bool score_anchor(const float *rc, int stride, int d, int s, float te,
-                                             const Series &pe, float nz, float rhs, float alpha,
-                                             float *score_out, float *w_out)
+__device__ __forceinline__ AnchorEval eval_anchor(const float *rc, int stride, int d, int s, float te, const Series &pe)
 {
     const float rs = rc[s * stride];
     float ne = 0.0f, num = 0.0f;
@@ -94,22 +96,108 @@ __device__ __forceinline__ bool score_anchor(const float *rc, int stride, int d,
         ne += q;
         num += rl * q;
     }
-    const float w = num / ne;
+    AnchorEval E;
+    E.ne = ne;
+    E.w = num / ne;
     float lhs = 0.0f;
 #pragma unroll 1
-    for (int l = 0; l < d; ++l) lhs += fabsf(rc[l * stride] - w);
-    const float score = ne - nz;
+    for (int l = 0; l < d; ++l) lhs += fabsf(rc[l * stride] - E.w);
+    E.lhs = lhs;
+    return E;
+}
+
+// Alg. 2's pass test: l1 decrease over the column and n_e - n_z >= alpha.
+template <bool IND>
+__device__ __forceinline__ bool score_anchor(const float *rc, int stride, int d, int s, float te,
+                                             const Series &pe, float nz, float rhs, float alpha,
+                                             float *score_out, float *w_out)
+{
+    const AnchorEval E = eval_anchor<IND>(rc, stride, d, s, te, pe);
+    const float score = E.ne - nz;
     *score_out = score;
-    *w_out = w;
-    return lhs <= rhs && score >= alpha;
+    *w_out = E.w;
+    return E.lhs <= rhs && score >= alpha;
+}
+
+// ---------------------------------------------------------------------------
+// Learned column scorer: a 16 -> 32 -> 32 -> 1 MLP (ReLU) on per-candidate
+// features; its logit replaces the test n_e - n_z >= alpha.  Parameters, in
+// this order: W1[i*32+o] (16x32), b1[32], W2[i*32+o] (32x32), b2[32], w3[32], b3.
+// ---------------------------------------------------------------------------
+#define RL0_NFEAT 16
+#define RL0_HID 32
+#define RL0_OFF_W1 0
+#define RL0_OFF_B1 (RL0_OFF_W1 + RL0_NFEAT * RL0_HID)
+#define RL0_OFF_W2 (RL0_OFF_B1 + RL0_HID)
+#define RL0_OFF_B2 (RL0_OFF_W2 + RL0_HID * RL0_HID)
+#define RL0_OFF_W3 (RL0_OFF_B2 + RL0_HID)
+#define RL0_OFF_B3 (RL0_OFF_W3 + RL0_HID)
+static_assert(RL0_OFF_B3 + 1 == RL0_MLP_PARAMS, "parameter layout");
+#define RL0_DEV_CLIP 8.0f
+
+// Features of a candidate (column residuals rc, anchor evaluation E, n_z, rhs):
+//  f0..f6  the 7 smallest |r_l - w| / sigma_n, clipped at 8 (8 pads d < 7)
+//  f7 n_e/d, f8 n_z/d, f9 log(1 + |w|/sigma_n)/5, f10 l1 gain (rhs - lhs)/rhs in [-1, 1],
+//  f11 t, f12 d rho, f13 (n_e - n_z)/d, f14 = f15 = 0.
+__device__ __forceinline__ void candidate_features(const float *rc, int stride, int d, const AnchorEval &E, float nz,
+                                                   float rhs, float inv_sn, float t, float drho, float *f)
+{
+    unsigned used = 0u;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        float best = RL0_DEV_CLIP;
+        int bi = -1;
+#pragma unroll 1
+        for (int l = 0; l < d; ++l) {
+            if ((used >> l) & 1u) continue;
+            const float v = fminf(fabsf(rc[l * stride] - E.w) * inv_sn, RL0_DEV_CLIP);
+            if (v < best) { best = v; bi = l; }
+        }
+        if (bi >= 0) used |= 1u << bi;
+        f[q] = best;
+    }
+    const float invd = 1.0f / (float)d;
+    f[7] = E.ne * invd;
+    f[8] = nz * invd;
+    f[9] = log1pf(fabsf(E.w) * inv_sn) * 0.2f;
+    f[10] = fminf(fmaxf((rhs - E.lhs) / fmaxf(rhs, 1e-30f), -1.0f), 1.0f);
+    f[11] = t;
+    f[12] = drho;
+    f[13] = (E.ne - nz) * invd;
+    f[14] = 0.0f;
+    f[15] = 0.0f;
+}
+
+// Logit of the MLP with parameters W (FP32 copies of the BF16 weights).
+__device__ __forceinline__ float mlp_logit(const float *W, const float *f)
+{
+    float h1[RL0_HID];
+#pragma unroll
+    for (int o = 0; o < RL0_HID; ++o) {
+        float acc = W[RL0_OFF_B1 + o];
+#pragma unroll
+        for (int i = 0; i < RL0_NFEAT; ++i) acc = fmaf(f[i], W[RL0_OFF_W1 + i * RL0_HID + o], acc);
+        h1[o] = fmaxf(acc, 0.0f);
+    }
+    float out = W[RL0_OFF_B3];
+#pragma unroll 4
+    for (int o = 0; o < RL0_HID; ++o) {
+        float acc = W[RL0_OFF_B2 + o];
+#pragma unroll
+        for (int i = 0; i < RL0_HID; ++i) acc = fmaf(h1[i], W[RL0_OFF_W2 + i * RL0_HID + o], acc);
+        out = fmaf(fmaxf(acc, 0.0f), W[RL0_OFF_W3 + o], out);
+    }
+    return out;
 }
 
 // Fast-path bound of Alg. 2's test for every anchor of a column held in
-// registers: the anchors (|r_i| >= ta) whose n_e can still reach
-// n_z + alpha, with n_e <= 1 + #{l != i : |r_i - r_l| <= reach}.
+// registers: the anchors (|r_i| >= ta) whose n_e can still reach n_z + need,
+// with n_e <= 1 + #{l != i : |r_i - r_l| <= reach}.  Callers pass
+// need = alpha for the 0/1 scores (exact counts) and alpha - 1e-3 for the
+// continuous ones (FP32 sums of values <= 1).
 template <int DMAX, bool IND>
 __device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, float ta, float reach, float nz,
-                                                      float alpha)
+                                                      float need)
 {
     unsigned amask = 0;
 #pragma unroll
@@ -129,7 +217,6 @@ __device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, flo
             }
         }
     }
-    const float need = IND ? alpha : alpha - 1e-3f;
     unsigned cand = 0;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)

@@ -227,7 +227,8 @@ int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolv
     if (p.noiseless_tol == 0.0) p.noiseless_tol = 1e-5;
     if (!(p.noiseless_tol > 0.0)) return RL0_ERR_INVALID_ARG;
     if (p.scorer != 0 && p.scorer != 1) return RL0_ERR_INVALID_ARG;
-    if (p.scorer == 1 && !p.mlp) return RL0_ERR_INVALID_ARG;
+    if (p.scorer == 1 && (!p.mlp || !(p.sigma_n > 0.0) || d > 16)) return RL0_ERR_INVALID_ARG;
+    if (p.scorer == 1 && !(p.mlp_threshold >= 0.0 && p.mlp_threshold < 1.0)) return RL0_ERR_INVALID_ARG;
     if (p.profile != 0 && p.profile != 1) return RL0_ERR_INVALID_ARG;
     // reading: t_r = 1 - r c for every r >= 0 with t_r > 0 (counted with a
     // tolerance so that c = 0.025 gives exactly 40 rounds)
@@ -260,7 +261,12 @@ void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx,
     ctx->stop_rel = R.stop_rel;
     ctx->scorer = p.scorer;
     ctx->mlp = p.mlp;
-    ctx->mlp_threshold = (float)(p.mlp_threshold == 0.0 ? 0.5 : p.mlp_threshold);
+    const double th = (p.mlp_threshold == 0.0) ? 0.5 : p.mlp_threshold;
+    ctx->mlp_threshold = (float)th;
+    ctx->logit_thr = (float)std::log(th / (1.0 - th));
+    ctx->learned_need = 1.5f;
+    ctx->inv_sn = (p.sigma_n > 0.0) ? (float)(1.0 / p.sigma_n) : 0.0f;
+    ctx->drho = (float)(d * rho);
     HostSeries hz, he;
     if (p.sigma_n > 0.0) {
         hz = make_series(d * rho, s2, n2, p.ell);

@@ -1,0 +1,174 @@
+"""GPU learned column scorer: gradients and forward against the FP64 oracle, candidate
+features against the oracle's definition, the learned rule reducing to Algorithm 2's rule
+for analytic-equivalent weights, learned decodes against the oracle's learned decode, and
+what a network trained on the method's own decode logs gains over the analytic rule."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gm
+import oracle
+from oracle import mlp as omlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from test_oracle_mlp import analytic_equivalent_bf16  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rl0():
+    import paper_1704_09012_gb300 as m
+    m._lib()
+    return m
+
+
+def _A(rows, m):
+    n, d = rows.shape
+    return sp.csr_matrix((np.ones(n * d), (rows.ravel(), np.repeat(np.arange(n), d))), shape=(m, n))
+
+
+def _problem(n, m, k, d, sigma_n, seed):
+    I = gm.instance(n, m, k, d, sigma_n, seed)
+    y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
+    return I, y.astype(np.float32)
+
+
+def test_mlp_gradient_matches_oracle(rl0):
+    rng = np.random.default_rng(0)
+    N = 5000
+    F = rng.standard_normal((N, 16)).astype(np.float32)
+    y = (rng.random(N) < 0.3).astype(np.float32)
+    w = rl0.mlp_init(seed=7)
+    loss, g = rl0.mlp_grad(w, torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda())
+    Lo, go = omlp.loss_and_grad(w.cpu().numpy().astype(np.float64), F.astype(np.float64), y.astype(np.float64))
+    assert loss == pytest.approx(Lo, rel=1e-6)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - go)) <= 1e-4 * np.max(np.abs(go))
+    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go)
+    # the library's gradient is deterministic
+    _, g2 = rl0.mlp_grad(w, torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda())
+    assert np.array_equal(g, g2.cpu().numpy().astype(np.float64))
+
+
+def test_mlp_forward_matches_oracle_with_bf16_weights(rl0):
+    rng = np.random.default_rng(1)
+    F = rng.standard_normal((3000, 16)).astype(np.float32)
+    w = rl0.mlp_init(seed=3)
+    wb = rl0.mlp_export(w)
+    lg = rl0.mlp_forward(wb, torch.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
+    bits = wb.cpu().numpy().view(np.uint16)
+    Wf = oracle.bf16_to_f64(bits)
+    ref = oracle.mlp_logits(Wf, F.astype(np.float64))
+    assert np.max(np.abs(lg - ref)) <= 1e-5 * (1 + np.max(np.abs(ref)))
+    # BF16 rounding of the FP32 parameters is round-to-nearest-even
+    w32 = w.cpu().numpy()
+    assert np.all(np.abs(Wf - w32) <= np.abs(w32) * 2.0 ** -8)
+
+
+def test_candidate_features_match_the_oracle_definition(rl0):
+    I, y32 = _problem(4096, 1024, 100, 7, 1e-3, 5)
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
+    rng = np.random.default_rng(2)
+    x = I.x.astype(np.float64).copy()
+    sh = rng.choice(I.support, 40, replace=False)
+    x[sh] += rng.uniform(0.2, 1.0, sh.size)
+    x[rng.choice(I.support, 30, replace=False)] = 0.0
+    x32 = x.astype(np.float32)
+    r32 = (y32.astype(np.float64) - _A(I.rows, I.m) @ x32.astype(np.float64)).astype(np.float32)
+    ridx = 12
+    f, meta, w = rl0.candidate_features(A, torch.from_numpy(y32).cuda(), I.k, ridx, torch.from_numpy(x32).cuda(),
+                                        torch.from_numpy(r32).cuda(), sigma_n=I.sigma_n)
+    f = f.cpu().numpy().astype(np.float64)
+    meta = meta.cpu().numpy()
+    assert f.shape[0] > 20
+    c = oracle.default_c(False, I.m / I.n, I.k / I.m)
+    t = 1 - ridx * c
+    rho = I.k / I.m
+    r = r32.astype(np.float64)
+    checked = 0
+    for e in range(f.shape[0]):
+        j, s = int(meta[e, 0]), int(meta[e, 1])
+        rl = r[I.rows[j]]
+        lz = oracle.log_posterior("z", rl, I.d, rho, 1.0, I.sigma_n)
+        assert lz[s] <= math.log(1 - t) + 1e-12              # an anchor
+        qe = np.exp(oracle.log_posterior("e", rl[s] - rl, I.d, rho, 1.0, I.sigma_n))
+        ne, nz = qe.sum(), np.exp(lz).sum()
+        wv = (rl * qe).sum() / ne
+        lhs, rhs = np.abs(rl - wv).sum(), np.abs(rl).sum()
+        assert ne - nz >= 1.5 - 1e-4
+        fo = oracle.features(rl, wv, ne, nz, lhs, rhs, I.sigma_n, t, I.d * rho)
+        np.testing.assert_allclose(f[e], fo, rtol=2e-4, atol=2e-4)
+        checked += 1
+    assert checked == f.shape[0]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_learned_rule_with_analytic_weights_equals_analytic_decode(rl0, seed):
+    I, y32 = _problem(3000, 800, 60, 8, 2e-3, seed)
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
+    bits = analytic_equivalent_bf16(I.d)
+    wb = torch.from_numpy(bits.view(np.int16)).cuda()
+    y = torch.from_numpy(y32).cuda()
+    xa, sa = rl0.decode(A, y, I.k, sigma_n=I.sigma_n)
+    xl, sl = rl0.decode(A, y, I.k, sigma_n=I.sigma_n, scorer=1, mlp=wb)
+    xa, xl = xa.cpu().numpy().astype(np.float64), xl.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.nonzero(xl)[0], np.nonzero(xa)[0])
+    assert np.linalg.norm(xl - xa) <= 1e-5 * np.linalg.norm(xa)
+    xo, so, _ = oracle.decode(I.rows, y32.astype(np.float64), I.k, sigma_n=I.sigma_n, mlp_bf16=bits)
+    assert np.array_equal(np.nonzero(xl)[0], np.nonzero(xo)[0])
+    assert np.linalg.norm(xl - xo) <= 1e-5 * np.linalg.norm(xo)
+
+
+def _success(x, xt, m, sn):
+    xl1 = np.abs(xt).sum()
+    tol = min((m * sn * math.sqrt(2 / math.pi) + math.sqrt(m * sn * sn * (1 - 2 / math.pi))) / xl1, 0.1)
+    return np.abs(x - xt).sum() / xl1 <= tol
+
+
+def test_trained_scorer_against_the_analytic_rule(rl0):
+    from paper_1704_09012_gb300 import learned
+    rng = np.random.default_rng(11)
+    n, d = 1 << 14, 7
+    F, Y = [], []
+    for i in range(12):                                   # decode logs of the method itself
+        m = int(0.1 * n)
+        rho = float(rng.uniform(0.1, 0.2))
+        k = int(rho * m)
+        sn = gm.sigma_from_snr(d, k / m, float(rng.uniform(30, 40)))
+        I, y32 = _problem(n, m, k, d, sn, 500 + i)
+        A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), m)
+        f, lab = learned.decode_log_samples(A, torch.from_numpy(y32).cuda(), k, torch.from_numpy(I.x).cuda(), sn)
+        F.append(f)
+        Y.append(lab)
+    F, Y = torch.cat(F), torch.cat(Y)
+    assert F.shape[0] > 2000 and 0.05 < float(Y.mean()) < 0.95
+    wb, w, loss = learned.train_scorer(F, Y, epochs=10)
+    assert loss < 0.5
+    # held-out instances: recovery and rounds, learned vs analytic
+    res = []
+    for i in range(8):
+        m = int(0.1 * n)
+        rho = float(rng.uniform(0.1, 0.2))
+        k = int(rho * m)
+        sn = gm.sigma_from_snr(d, k / m, float(rng.uniform(30, 40)))
+        I, y32 = _problem(n, m, k, d, sn, 900 + i)
+        A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), m)
+        y = torch.from_numpy(y32).cuda()
+        xa, sa = rl0.decode(A, y, k, sigma_n=sn)
+        xl, sl = rl0.decode(A, y, k, sigma_n=sn, scorer=1, mlp=wb)
+        res.append((_success(xa.cpu().numpy(), I.x, m, sn), _success(xl.cpu().numpy(), I.x, m, sn),
+                    sa["rounds"], sl["rounds"], sa["ms"], sl["ms"], sl["analytic_rounds"]))
+        if i == 0:                                        # the learned decode against the oracle's
+            bits = wb.cpu().numpy().view(np.uint16)
+            xo, so, _ = oracle.decode(I.rows, y32.astype(np.float64), k, sigma_n=sn, mlp_bf16=bits)
+            xg = xl.cpu().numpy().astype(np.float64)
+            assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+            assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
+    res = np.array(res, dtype=float)
+    print("analytic success %.2f rounds %.1f ms %.3f | learned success %.2f rounds %.1f ms %.3f (fallback rounds %.1f)"
+          % (res[:, 0].mean(), res[:, 2].mean(), res[:, 4].mean(), res[:, 1].mean(), res[:, 3].mean(),
+             res[:, 5].mean(), res[:, 6].mean()))
+    assert res[:, 1].mean() >= res[:, 0].mean()           # no loss of recovery
