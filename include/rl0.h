@@ -201,11 +201,13 @@ int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap);
 /* ---- Learned column scorer (an addition to the paper's method) ------------------------
  * A 16 -> 32 -> 32 -> 1 MLP with ReLU hidden layers whose logit replaces Algorithm 2's
  * consensus test n_e - n_z >= alpha when rl0_params.scorer = 1: an anchor passes when
- * the l1 test holds, n_e - n_z >= 1.5 and logit >= log(mlp_threshold / (1 - mlp_threshold)),
- * and the column takes its passing anchor of largest logit.  Features, in this order: the 7 smallest |r_l - w| / sigma_n
+ * the l1 test holds, n_e - n_z >= 1.5 and logit >= log(mlp_threshold / (1 - mlp_threshold));
+ * as with the analytic rule, the last passing anchor in row order gives the update.
+ * Features, in this order: the 7 smallest |r_l - w| / sigma_n
  * (clipped at 8, padded with 8), n_e/d, n_z/d, log(1 + |w|/sigma_n)/5, the column's
  * relative l1 gain (clipped to [-1, 1]), t, d k/m, (n_e - n_z)/d, 0, 0.  If the learned
- * decode ends unconverged, the analytic decode continues from its x_hat.
+ * decode ends with ||r||_1 > E||eta||_1 + 3 sqrt(Var||eta||_1), the analytic decode
+ * continues from its x_hat.
  * Parameters: RL0_MLP_PARAMS (= 1633) values, W1 (16x32, input-major), b1 (32),
  * W2 (32x32), b2 (32), w3 (32), b3; FP32 for training, BF16 for decoding. */
 #define RL0_MLP_PARAMS 1633

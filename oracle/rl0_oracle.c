@@ -534,10 +534,10 @@ typedef struct {
  * Every column reads only rh (Jacobi: updates of this round are not seen).
  *
  * readings:
- *  - the update x'_j <- x'_j + w is applied once per column, with the passing
- *    anchor of largest n_e - n_z (ties to the lowest slot), because every
- *    member of a consensus group passes the test and would otherwise add w
- *    up to d times (Alg. 1 likewise assigns a single u_j);
+ *  - the update x'_j <- x'_j + w is applied once per column, because every
+ *    member of a consensus group passes the test and would otherwise add w up
+ *    to d times; the value is that of the last passing anchor in row order,
+ *    the overwrite semantics of Alg. 1's u_j <- r_i;
  *  - ||r - w e_i||_1 <= ||r||_1 is read over the column's rows N(j):
  *    sum_l |r_l - w| <= sum_l |r_l|, the l1 change that adding w to x_j
  *    alone would cause (literal_ei_test = 1 keeps the printed |r_i - w| <= |r_i|);
@@ -597,8 +597,7 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
             }
             if (slack < margin) margin = slack;
             if (p->learned) {
-                /* learned rule: l1 test, n_e - n_z >= 1.5, logit >= logit(threshold);
-                 * the column takes its passing anchor of largest logit */
+                /* learned rule: l1 test, n_e - n_z >= 1.5, logit >= logit(threshold) */
                 if (lhs <= rhs && score >= 1.5) {
                     double f[ORC_NFEAT];
                     orc_features(d, rl, w, ne, nz, lhs, rhs, p->sigma_n, t, P->drho, f);
@@ -609,10 +608,10 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                     if (ml < margin) margin = ml;
                     double m3 = fabs(score - 1.5);
                     if (m3 < margin) margin = m3;
-                    if (lg >= lt && (best < 0 || lg > best_score)) { best = s; best_score = lg; best_w = w; }
+                    if (lg >= lt) { best = s; best_score = lg; best_w = w; }
                 }
             } else if (lhs <= rhs && score >= p->alpha) {
-                if (best < 0 || score > best_score) { best = s; best_score = score; best_w = w; }
+                best = s; best_score = score; best_w = w;
             }
         }
         if (best >= 0) { xp[j] = xh[j] + best_w; upd++; }
@@ -698,9 +697,12 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
         rounds++;
     }
     int analytic_rounds = 0;
-    if (!rc && p.learned && !(l1h <= stop)) {
-        /* not converged with the learned scorer: the analytic rule continues
-         * from x_hat with a fresh sweep from t = 1 */
+    /* the learned decode is kept when its residual is consistent with the noise,
+     * ||r||_1 <= E||eta||_1 + 3 sqrt(Var||eta||_1) (Section "Stopping conditions");
+     * otherwise the analytic rule continues from x_hat with a fresh sweep */
+    double keep_level = (double)m * p.sigma_n * sqrt(2.0 / ORC_PI) +
+                        3.0 * sqrt((double)m * p.sigma_n * p.sigma_n * (1.0 - 2.0 / ORC_PI));
+    if (!rc && p.learned && !(l1h <= keep_level)) {
         orc_params p2 = p;
         p2.learned = 0;
         orc_matvec(n, m, d, rows, xhat, rh);

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                     s_rhs[tid] = rhs;
                 }
                 int best = -1;
-                float bscore = 0.0f, bw = 0.0f;
+                float bw = 0.0f;
                 while (__syncthreads_or(cand != 0u)) {
                     int my = -1, ms = 0;
                     if (cand) {
@@ -184,9 +184,8 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                         s_w[e] = w;
                     }
                     __syncthreads();
-                    if (my >= 0 && s_ok[my] && (best < 0 || s_score[my] > bscore)) {
+                    if (my >= 0 && s_ok[my]) {      // the last passing anchor in row order stands
                         best = ms;
-                        bscore = s_score[my];
                         bw = s_w[my];
                     }
                     if (tid == 0) S.nq = 0;

@@ -164,6 +164,7 @@ struct Resolved {
     int nrounds;
     int indicator;
     double stop_level, stop_rel;
+    double keep_level;        // learned decodes end without the analytic continuation below this
 };
 HostSeries make_series(double lam, double s2, double vn, int ell);
 double series_F(const HostSeries &H, double w);

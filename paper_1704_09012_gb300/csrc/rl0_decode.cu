@@ -7,7 +7,7 @@
 //   column_score  every column j reads its d residuals (slot-major row ids,
 //                 one coalesced 4-byte load per slot per thread, L2 gathers of
 //                 (r, p_z(r))), scores every anchor (Table "scores",
-//                 Eqs. (ne_nz_1), (ne_nz_2)), applies the best passing update
+//                 Eqs. (ne_nz_1), (ne_nz_2)), applies the last passing update
 //                 to x in place and logs it for undo;
 //   hk_select     H_k on the list of nonzeros (single CTA radix select on the
 //                 63-bit key (|x_j| bits, ~j): ties go to the smaller j);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     // candidates are scored by the whole CTA, one per column per pass, each
     // column's candidates in slot order
     int best = -1;
-    float bscore = 0.0f, bw = 0.0f;
+    float bw = 0.0f;
     while (__syncthreads_or(cand != 0u)) {
         int my = -1, ms = 0;
         if (cand) {
@@ -278,9 +278,8 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             }
         }
         __syncthreads();
-        if (my >= 0 && s_ok[my] && (best < 0 || s_score[my] > bscore)) {
+        if (my >= 0 && s_ok[my]) {                  // the last passing anchor in row order stands
             best = ms;
-            bscore = s_score[my];
             bw = s_w[my];
         }
         if (tid == 0) s_nq = 0;
@@ -1005,9 +1004,10 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     }
     A->last_log_rounds = H->st.rounds_run;
     if (H->st.status) return RL0_ERR_TIMEOUT;
-    if (learned && !H->st.converged) {
-        // Not converged with the learned scorer: Algorithm 2 with the analytic
-        // scores continues from the learned x_hat (a fresh sweep from t = 1).
+    if (learned && !(H->st.l1_hat <= R.keep_level)) {
+        // The learned decode's residual is not consistent with the noise
+        // (||r||_1 > E||eta||_1 + 3 sqrt(Var||eta||_1)): Algorithm 2 with the
+        // analytic scores continues from the learned x_hat (a fresh sweep).
         const DecodeState first = H->st;
         Resolved R2 = R;
         R2.p.scorer = 0;

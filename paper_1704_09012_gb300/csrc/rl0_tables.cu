@@ -242,6 +242,8 @@ int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolv
     // reading: noiseless decodes stop at ||r||_1 <= tol ||y||_1
     R->stop_level = (p.sigma_n > 0.0) ? (double)m * p.sigma_n * std::sqrt(2.0 / M_PI) : 0.0;
     R->stop_rel = (p.sigma_n > 0.0) ? 0.0 : p.noiseless_tol;
+    // learned decodes: a residual consistent with the noise, E||eta||_1 + 3 sqrt(Var||eta||_1)
+    R->keep_level = R->stop_level + 3.0 * std::sqrt((double)m * p.sigma_n * p.sigma_n * (1.0 - 2.0 / M_PI));
     return RL0_OK;
 }
 

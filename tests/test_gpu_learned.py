@@ -165,7 +165,8 @@ def test_training_reduces_the_loss(rl0, trained):
     # the exported BF16 network separates the labels on its training logs
     lg = rl0.mlp_forward(trained["wb"], F)
     acc = float(((lg >= 0).float() == Y).float().mean())
-    assert acc > 0.85
+    base = max(float(Y.mean()), 1 - float(Y.mean()))
+    assert acc > base + 0.02
 
 
 def test_learned_round_step_matches_oracle(rl0, trained):

@@ -340,8 +340,7 @@ def _python_round(I, y, xh, rh, t, quantised, alpha):
             ne, nzv = qe.sum(), qz.sum()
             w = (rl * qe).sum() / ne
             if np.abs(rl - w).sum() <= np.abs(rl).sum() and ne - nzv >= alpha:
-                if best is None or ne - nzv > best[0]:
-                    best = (ne - nzv, w)
+                best = (ne - nzv, w)                  # the last passing anchor stands
         if best is not None:
             xp[j] = xh[j] + best[1]
     nz = np.nonzero(xp)[0]
