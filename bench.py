@@ -187,6 +187,65 @@ def bench_batched(rl0, torch, count, steps, flush, plain=True):
     return res
 
 
+def bench_learned(rl0, torch, flush, train_instances=4, eval_instances=2):
+    """The learned column scorer: trained on the decode logs of analytic decodes at
+    n=2^20, d=7, delta=0.1, rho~U[0.1,0.2], SNR~U[30,40] dB, then evaluated against the
+    analytic rule at n=2^22, delta=0.1, rho=0.15, SNR 30 dB (time to recover, rounds,
+    success condition of Section 'Stopping conditions')."""
+    import numpy as np
+    import gm
+    from paper_1704_09012_gb300 import learned
+    rng = np.random.default_rng(2024)
+    d = 7
+    F, Y = [], []
+    t0 = time.perf_counter()
+    for i in range(train_instances):
+        n = 1 << 20
+        m = int(0.1 * n)
+        k = int(float(rng.uniform(0.1, 0.2)) * m)
+        sn = gm.sigma_from_snr(d, k / m, float(rng.uniform(30, 40)))
+        A = rl0.Expander.random(n, m, d, seed=70000 + i)
+        x, _ = gm.draw_signal(n, k, 1.0, 70000 + i)
+        xt = torch.from_numpy(x).cuda()
+        y = rl0.sketch(A, xt, sigma_n=sn, noise_seed=71000 + i)
+        f, lab = learned.decode_log_samples(A, y, k, xt, sn)
+        F.append(f)
+        Y.append(lab)
+        A.free()
+    F, Y = torch.cat(F), torch.cat(Y)
+    wb, _, loss = learned.train_scorer(F, Y, epochs=8)
+    t_train = time.perf_counter() - t0
+    res = {"workload": "train: %d analytic decodes at n=2^20 (d=7, delta=0.1, rho~U[0.1,0.2], SNR~U[30,40] dB), "
+                       "%d logged candidates; evaluate: n=2^22, delta=0.1, rho=0.15, SNR 30 dB, %d instances"
+                       % (train_instances, F.shape[0], eval_instances),
+           "train_loss": loss, "train_s": t_train}
+    n = 1 << 22
+    m = int(0.1 * n)
+    k = int(0.15 * m)
+    sn = gm.sigma_from_snr(d, k / m, 30.0)
+    rows = {"analytic": [], "learned": []}
+    for i in range(eval_instances):
+        A = rl0.Expander.random(n, m, d, seed=80000 + i)
+        x, _ = gm.draw_signal(n, k, 1.0, 80000 + i)
+        y = rl0.sketch(A, torch.from_numpy(x).cuda(), sigma_n=sn, noise_seed=81000 + i)
+        for name, extra in (("analytic", {}), ("learned", {"scorer": 1, "mlp": wb})):
+            rl0.decode(A, y, k, sigma_n=sn, **extra)
+            flush.zero_()
+            xh, st = rl0.decode(A, y, k, sigma_n=sn, **extra)
+            xr = xh.cpu().numpy().astype(np.float64)
+            xl1 = np.abs(x).sum()
+            tol = min((m * sn * math.sqrt(2 / math.pi) + math.sqrt(m * sn * sn * (1 - 2 / math.pi))) / xl1, 0.1)
+            rows[name].append((st["ms"], st["rounds"], float(np.abs(xr - x).sum() / xl1 <= tol),
+                               float(np.abs(xr - x).sum() / xl1)))
+        A.free()
+    for name, v in rows.items():
+        v = np.array(v)
+        res[name] = {"ms_to_recover": float(v[:, 0].mean()), "rounds": float(v[:, 1].mean()),
+                     "success_rate": float(v[:, 2].mean()), "rel_l1_err": float(v[:, 3].mean()),
+                     "value": float(n * d * v[:, 1].mean() / (v[:, 0].mean() * 1e-3)), "unit": UNIT}
+    return res
+
+
 def cpu_baseline(cfg, seed, budget_s=20.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample: full-size rounds
     from the start of the decode (x_hat = 0) until the time budget is spent."""
@@ -263,6 +322,7 @@ def main():
     ap.add_argument("--quantised", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=4096, help="instances of the batched sub-measurement (0: skip)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-scorer sub-measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -388,6 +448,8 @@ def main():
     }
     if args.batched > 0:
         line["batched"] = bench_batched(rl0, torch, args.batched, max(1, min(args.steps, 3)), flush)
+    if not args.no_learned:
+        line["learned"] = bench_learned(rl0, torch, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, seed)
     if rank == 0:

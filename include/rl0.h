@@ -79,13 +79,13 @@ typedef struct {
     float   ms;                /* device time of the decode (CUDA events), milliseconds      */
     int     hk_rounds;         /* rounds in which H_k had to drop entries                    */
     int     fallback_rounds;   /* rounds whose residual took the full CSR rebuild            */
-    /* profile = 1 only: summed device time of each kernel group over the rounds, and
-     * the number of kernel launches of the decode (all rounds of the replayed graph) */
+    /* profile = 1 only: summed device time of each kernel group over the rounds the decode
+     * ran (event nodes around the groups, so each interval includes the launch gap) */
     float   ms_score;          /* column scoring                                             */
     float   ms_hk;             /* H_k selection                                              */
     float   ms_rebuild;        /* scatter + residual rebuild                                 */
     float   ms_accept;         /* accept / undo                                              */
-    int     launches;          /* kernels launched by the decode                             */
+    int     launches;          /* kernels launched by the decode (any mode)                  */
     int     analytic_rounds;   /* scorer = 1: rounds of the analytic continuation (0 if the  */
                                /* learned decode converged on its own)                       */
 } rl0_stats;

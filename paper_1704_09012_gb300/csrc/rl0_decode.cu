@@ -990,7 +990,8 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         stats->launches = launches_per_decode(prof ? R.nrounds : H->st.rounds_run);
         if (prof) {
             float acc[4] = {0, 0, 0, 0};
-            for (int r = 0; r < R.nrounds; ++r)
+            const int active = H->st.rounds_run < R.nrounds ? H->st.rounds_run : R.nrounds;
+            for (int r = 0; r < active; ++r)            // rounds after the decode finished only exit
                 for (int q = 0; q < 4; ++q) {
                     float v = 0.0f;
                     if (cudaEventElapsedTime(&v, E->events[4 * r + q], E->events[4 * r + q + 1]) == cudaSuccess)
