@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                 while (__syncthreads_or(cand != 0u)) {
                     int my = -1, ms = 0;
                     if (cand) {
-                        ms = __ffs(cand) - 1;
-                        cand &= cand - 1u;
+                        ms = 31 - __clz(cand);      // highest remaining slot first
+                        cand &= ~(1u << ms);
                         my = atomicAdd(&S.nq, 1);
                         s_q[my] = (unsigned short)((tid << 5) | ms);
                     }
@@ -184,9 +184,10 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                         s_w[e] = w;
                     }
                     __syncthreads();
-                    if (my >= 0 && s_ok[my]) {      // the last passing anchor in row order stands
+                    if (my >= 0 && s_ok[my]) {      // first pass from the top = last passing anchor
                         best = ms;
                         bw = s_w[my];
+                        cand = 0u;
                     }
                     if (tid == 0) S.nq = 0;
                 }

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
         for (int p = tid; p < RL0_MLP_PARAMS; p += NT) s_W[p] = __bfloat162float(wb[p]);
     }
-    __syncthreads();
+    // (the shared copies above are first read after the candidate loop's barrier)
     const int n = a.n, d = a.d;
     const int j = blockIdx.x * NT + tid;
     const bool active = j < n;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         }
     }
     const float need = LEARNED ? (IND ? ctx->learned_need : ctx->learned_need - 1e-3f) : (IND ? alpha : alpha - 1e-3f);
-    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, need) : 0u;
+    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : ctx->pe.cut, nz, need) : 0u;
     if (cand) {
 #pragma unroll
         for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
@@ -209,14 +209,14 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         s_rhs[tid] = rhs;
     }
     // candidates are scored by the whole CTA, one per column per pass, each
-    // column's candidates in slot order
+    // column's from its highest slot down until one passes
     int best = -1;
     float bw = 0.0f;
     while (__syncthreads_or(cand != 0u)) {
         int my = -1, ms = 0;
         if (cand) {
-            ms = __ffs(cand) - 1;
-            cand &= cand - 1u;
+            ms = 31 - __clz(cand);                  // highest remaining slot first
+            cand &= ~(1u << ms);
             my = atomicAdd(&s_nq, 1);
             s_q[my] = (unsigned short)((tid << 5) | ms);
         }
@@ -278,9 +278,10 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             }
         }
         __syncthreads();
-        if (my >= 0 && s_ok[my]) {                  // the last passing anchor in row order stands
-            best = ms;
+        if (my >= 0 && s_ok[my]) {                  // the first pass from the top is the last passing
+            best = ms;                              // anchor in row order: it stands, the rest is moot
             bw = s_w[my];
+            cand = 0u;
         }
         if (tid == 0) s_nq = 0;
     }
