@@ -71,6 +71,8 @@ struct DecodeState {
     int nnz_delta;            // change of the nonzero count made by this round's updates
     unsigned zeroed;          // updates that made an entry exactly zero this round
     unsigned iters;           // accept invocations (bounds the graph's while loop)
+    unsigned col_done;        // CTAs of the column kernel finished (last one applies H_k)
+    unsigned rb_done;         // CTAs of the rebuild finished (last one accepts or undoes)
     int rounds_run;
     int accepted_rounds;
     int hk_rounds;
@@ -103,6 +105,7 @@ struct DecodeCtx {
     float drho;               // d k / m
     int32_t *passed;          // optional per-column pass flags (round_step)
     int want_log;
+    int no_accept;            // round_step: stop after the rebuild (no accept, no undo)
 };
 
 struct UndoEntry {

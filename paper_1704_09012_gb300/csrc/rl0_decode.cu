@@ -322,26 +322,22 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             if (fresh) a.list[base + __popc(mask & ((1u << lane) - 1u))] = j;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// H_k: keep the k entries of largest |x'_j| (ties -> smaller j); single CTA.
-// Radix select of the k-th largest 63-bit key (bits(|x|) << 32 | ~j) in six
-// passes of at most 11 bits, then zero (and log) everything below it.
-// ---------------------------------------------------------------------------
-#define HK_THREADS 1024
-
-__global__ void __launch_bounds__(HK_THREADS) k_hk_select(KArgs a)
-{
-    __shared__ HkShared sm;
-    __shared__ unsigned suf[HK_THREADS];
-    DecodeState *st = a.st;
-    if (st->done || st->upd_count == 0) return;
-    // |supp x'| is known from the counters: nothing to do when it is at most k
-    const long long nnz = (long long)st->nnz + st->nnz_delta;
-    const long long k = a.ctx->k;
-    if (nnz <= k) return;
-    cta_hk_select<HK_THREADS>(a.list, st->list_count, a.ctx->x, k, a.hkkey, a.dlog, &st->drop_count, sm, suf);
+    // ---- the launch's last CTA applies H_k when |supp x'| > k (state read past L1)
+    __shared__ HkShared s_hk;
+    __shared__ unsigned s_suf[NT];
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&a.st->col_done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    DecodeState *stw = a.st;
+    const unsigned upd = __ldcg(&stw->upd_count);
+    const long long nnz = (long long)__ldcg(&stw->nnz) + __ldcg(&stw->nnz_delta);
+    if (tid == 0) stw->col_done = 0u;
+    if (upd == 0 || nnz <= ctx->k) return;
+    cta_hk_select<NT>(a.list, __ldcg(&stw->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &stw->drop_count, s_hk, s_suf);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,61 +365,17 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a)
 }
 
 
-__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
-{
-    __shared__ double sh[RL0_ROWS_CHUNK];
-    DecodeState *st = a.st;
-    if (st->done || st->upd_count == 0) return;
-    const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
-    const DecodeCtx *ctx = a.ctx;
-    const float *x = ctx->x;
-    float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
-    double l1 = 0.0;
-    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    if (i < a.m) {
-        float sum = 0.0f;
-        if (csr) {
-            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
-            a.bcnt[i] = 0;
-        } else {
-            const int c = a.bcnt[i];
-            if (c > 0) {
-                static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
-                int js[RL0_BUCKET];
-#pragma unroll
-                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
-                sort8(js);                              // ascending column order
-#pragma unroll
-                for (int q = 0; q < RL0_BUCKET; ++q)
-                    if (q < c) sum += x[js[q]];
-                a.bcnt[i] = 0;
-            }
-        }
-        const float r = ctx->y[i] - sum;
-        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
-        rz[i] = make_float2(r, z);
-        l1 = fabs((double)r);
-    }
-    const double s = block_sum_f64(l1, sh);
-    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
-}
-
 // ---------------------------------------------------------------------------
-// Accept / undo and round control (single CTA).
+// Accept / undo and round control, run by one CTA of NT threads: the rebuild's
+// last CTA, or its CTA 0 when the round changed nothing.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_accept(KArgs a)
+template <int NT>
+__device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
 {
-    __shared__ unsigned shu[1024];
     __shared__ double s_l1;
     __shared__ int s_acc;
     DecodeState *st = a.st;
     const int t = threadIdx.x;
-    if (st->done) {
-        // never expected inside the loop; keeps the while-condition consistent
-        if (t == 0 && a.has_cond) cudaGraphSetConditional(a.cond, 0u);
-        return;
-    }
-    const unsigned upd = st->upd_count;
     const DecodeCtx *ctx = a.ctx;
     float *x = ctx->x;
     if (t == 0) s_acc = 0;
@@ -431,7 +383,7 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
         if (t < 32) {
             // ||r||_1 of the candidate: chunk partials combined in a fixed order
             double v = 0.0;
-            for (int c = t; c < a.nchunks; c += 32) v += a.l1part[c];
+            for (int c = t; c < a.nchunks; c += 32) v += __ldcg(a.l1part + c);
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
             if (t == 0) { s_l1 = v; s_acc = (v < st->l1_hat); }
         }
@@ -441,21 +393,21 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
                 // entries became zero: stable in-place compaction of the list
                 const unsigned total = st->list_count;
                 unsigned out = 0;
-                for (unsigned base = 0; base < total; base += 1024) {
+                for (unsigned base = 0; base < total; base += NT) {
                     const unsigned e = base + t;
                     int j = -1;
                     unsigned keep = 0;
                     if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
                     shu[t] = keep;
                     __syncthreads();
-                    for (int off = 1; off < 1024; off <<= 1) {
+                    for (int off = 1; off < NT; off <<= 1) {
                         const unsigned w = (t >= off) ? shu[t - off] : 0u;
                         __syncthreads();
                         shu[t] += w;
                         __syncthreads();
                     }
                     const unsigned incl = shu[t];
-                    const unsigned blk = shu[1023];
+                    const unsigned blk = shu[NT - 1];
                     __syncthreads();
                     if (keep) a.list[out + incl - 1] = j;
                     out += blk;
@@ -472,9 +424,9 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
             }
         } else {
             const unsigned nd = st->drop_count;
-            for (unsigned e = t; e < nd; e += 1024) x[a.dlog[e].j] = a.dlog[e].old;
+            for (unsigned e = t; e < nd; e += NT) x[a.dlog[e].j] = a.dlog[e].old;
             __syncthreads();
-            for (unsigned e = t; e < upd; e += 1024) x[a.ulog[e].j] = a.ulog[e].old;
+            for (unsigned e = t; e < upd; e += NT) x[a.ulog[e].j] = a.ulog[e].old;
             if (t == 0) st->list_count = st->shat_count;
         }
         __syncthreads();
@@ -507,6 +459,63 @@ __global__ void __launch_bounds__(1024) k_accept(KArgs a)
         if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds) st->done = 1;
         if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
     }
+}
+
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
+{
+    __shared__ double sh[RL0_ROWS_CHUNK];
+    __shared__ unsigned s_scan[RL0_ROWS_CHUNK];
+    __shared__ int s_last;
+    DecodeState *st = a.st;
+    if (st->done) return;
+    const int no_accept = a.ctx->no_accept;
+    const unsigned upd = st->upd_count;
+    if (upd == 0) {                                // nothing changed: r = r_hat, only t advances
+        if (blockIdx.x == 0 && !no_accept) accept_step<RL0_ROWS_CHUNK>(a, 0u, s_scan);
+        return;
+    }
+    const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
+    const DecodeCtx *ctx = a.ctx;
+    const float *x = ctx->x;
+    float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
+    double l1 = 0.0;
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    if (i < a.m) {
+        float sum = 0.0f;
+        if (csr) {
+            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
+            a.bcnt[i] = 0;
+        } else {
+            const int c = a.bcnt[i];
+            if (c > 0) {
+                static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
+                int js[RL0_BUCKET];
+#pragma unroll
+                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
+                sort8(js);                              // ascending column order
+#pragma unroll
+                for (int q = 0; q < RL0_BUCKET; ++q)
+                    if (q < c) sum += x[js[q]];
+                a.bcnt[i] = 0;
+            }
+        }
+        const float r = ctx->y[i] - sum;
+        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
+        rz[i] = make_float2(r, z);
+        l1 = fabs((double)r);
+    }
+    const double s = block_sum_f64(l1, sh);
+    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+    if (no_accept) return;
+    // ---- the launch's last CTA accepts or undoes the round
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&st->rb_done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->rb_done = 0u;
+    accept_step<RL0_ROWS_CHUNK>(a, upd, s_scan);
 }
 
 // ||y - A x_hat||_1 with every step in FP64 (the final residual-norm check).
@@ -631,8 +640,8 @@ struct GraphEntry {
     std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
 
-// Kernels one decode graph launches: prologue (3), 5 per round, final check (2).
-int launches_per_decode(int nrounds) { return 3 + 5 * nrounds + 2; }
+// Kernels one decode graph launches: prologue (3), 3 per round, final check (2).
+int launches_per_decode(int nrounds) { return 3 + 3 * nrounds + 2; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -689,10 +698,9 @@ int dmax_of(int d) { return d <= 8 ? 8 : (d <= 16 ? 16 : 32); }
 // The kernels of one round (shared by the graph and by round_step).
 void launch_round(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-    launch_column_score(a, dmax, indicator, learned, s);
-    k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
+    launch_column_score(a, dmax, indicator, learned, s);   // + H_k in its last CTA
     k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+    k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);     // + accept in its last CTA
 }
 
 // The round loop as a graph.  Normal decodes: prologue kernels, then a WHILE
@@ -759,7 +767,6 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
                 cudaSuccess) { rc = RL0_ERR_CUDA; break; }
             launch_round(a, dmax, indicator, learned, s);
-            k_accept<<<1, 1024, 0, s>>>(a);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
             if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_l1, a.nchunks, RL0_ROWS_CHUNK, &a, nullptr, 0)))
@@ -786,12 +793,10 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         e = mark(4 * r);
         launch_column_score(a, dmax, indicator, learned, s);
         if (e == cudaSuccess) e = mark(4 * r + 1);
-        k_hk_select<<<1, HK_THREADS, 0, s>>>(a);
         if (e == cudaSuccess) e = mark(4 * r + 2);
         k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
         k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
         if (e == cudaSuccess) e = mark(4 * r + 3);
-        k_accept<<<1, 1024, 0, s>>>(a);
     }
     if (e == cudaSuccess) e = mark(4 * nrounds);
     k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
@@ -1029,7 +1034,6 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         k_list_count_from_support<<<1, 32, 0, s>>>(a);
         for (int r = 0; r < R2.nrounds; ++r) {
             launch_round(a, dmax, R2.indicator, 0, s);
-            k_accept<<<1, 1024, 0, s>>>(a);
         }
         k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
         k_final_sum<<<1, 32, 0, s>>>(a);
@@ -1050,7 +1054,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
             stats->hk_rounds = first.hk_rounds + H->st.hk_rounds;
             stats->fallback_rounds = first.fallback_rounds + H->st.fallback_rounds;
             stats->analytic_rounds = H->st.rounds_run;
-            stats->launches += 4 + 5 * R2.nrounds + 2;
+            stats->launches += 4 + 3 * R2.nrounds + 2;
         }
     }
     return RL0_OK;
@@ -1133,6 +1137,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     H->ctx.x = xp_dev;
     H->ctx.want_log = 0;
     H->ctx.passed = passed_dev;
+    H->ctx.no_accept = 1;
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
@@ -1287,7 +1292,6 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     for (int r = 0; r < R.nrounds; ++r) {
         launch_round(a, dmax, R.indicator, R.p.scorer == 1, s);
-        k_accept<<<1, 1024, 0, s>>>(a);
     }
     k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
     k_final_sum<<<1, 32, 0, s>>>(a);
