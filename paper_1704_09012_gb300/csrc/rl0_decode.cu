@@ -28,6 +28,7 @@
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
 #include <cuda_bf16.h>
+#include <cooperative_groups.h>
 
 #define CK(call)                                          \
     do {                                                  \
@@ -52,6 +53,7 @@ struct KArgs {
     double *final_part;
     cudaGraphConditionalHandle cond;   // while-loop condition of the round graph
     int has_cond;
+    int dsm_sh, dsm_cluster, dsm_grid; // cluster column kernel: slice 2^sh rows, CTAs per cluster, grid (0: off)
 };
 
 // r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
@@ -143,49 +145,71 @@ __global__ void k_list_count_from_support(KArgs a)
 // |r_i - r_l| <= te for the 0/1 scores, or <= the 2^-40 cut of p_e for the
 // continuous scores, where n_e <= 1 + popc(mask).  An anchor whose bound
 // cannot reach n_e - n_z >= alpha is dropped here; for the 0/1 scores the
-// bound is n_e itself.  Slow path (rare): the surviving anchors, in slot
-// order, get the exact n_e, omega and l1 test from residuals kept in shared
-// memory, in the same order of operations for every launch shape.
+// bound is n_e itself.  Slow path (rare): the surviving anchors get the exact
+// n_e, omega and l1 test from residuals kept in shared memory, scored by the
+// whole CTA from each column's highest slot down until one passes (that one is
+// the last passing anchor in row order, whose omega the column takes).
+//
+// Two kernels share the tile body: k_column_score gathers (r_i, p_z(r_i))
+// from L2; k_column_score_dsm stages r_hat in the distributed shared memory of
+// a thread-block cluster (each CTA holds a 2^slice_shift-row slice) and
+// gathers with cluster-shared loads.
 // ---------------------------------------------------------------------------
-// Threads per CTA of the column kernel (its shared arrays scale with DMAX).
 template <int DMAX> struct ColBlock { static constexpr int value = DMAX <= 8 ? 256 : (DMAX <= 16 ? 128 : 64); };
+#define RL0_DSM_NT 1024
 
-template <int DMAX, bool IND, bool LEARNED>
-__global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
+// Shared memory of the column kernels.  H_k's scratch (used by the launch's
+// last CTA after its tiles) shares the bytes of the candidate queue.
+template <int DMAX, int NT, bool LEARNED>
+struct ColShared {
+    union {
+        struct {
+            float r[DMAX][NT];                 // residuals of columns with candidates
+            float nz[NT], rhs[NT];
+            unsigned short q[NT];              // this pass's queue: (column lane << 5) | slot
+            float score[NT], w[NT];
+            unsigned char ok[NT];
+            float f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the queued candidates
+            float h1[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];     // hidden layers of a 32-candidate slice
+            float h2[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];
+            unsigned char l1ok[LEARNED ? NT : 1];
+        } c;
+        struct {
+            HkShared hk;
+            unsigned suf[NT];
+        } h;
+    };
+    Series pe;
+    float W[LEARNED ? RL0_MLP_PARAMS : 1];     // learned scorer parameters (FP32 copies)
+    int nq;
+    int last;
+};
+
+template <int DMAX, bool IND, bool LEARNED, int NT>
+__device__ __forceinline__ void col_setup(const DecodeCtx *ctx, ColShared<DMAX, NT, LEARNED> &S)
 {
-    constexpr int NT = ColBlock<DMAX>::value;
-    __shared__ Series s_pe;
-    __shared__ float s_W[LEARNED ? RL0_MLP_PARAMS : 1];   // learned scorer parameters (FP32 copies)
-    __shared__ float s_f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the queued candidates
-    __shared__ float s_h1[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];     // hidden layers of a 32-candidate slice
-    __shared__ float s_h2[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];
-    __shared__ unsigned char s_l1ok[LEARNED ? NT : 1];
-    __shared__ float s_r[DMAX][NT];           // residuals of columns with candidates
-    __shared__ float s_nz[NT], s_rhs[NT];
-    __shared__ unsigned short s_q[NT];        // this pass's queue: (column lane << 5) | slot
-    __shared__ float s_score[NT], s_w[NT];
-    __shared__ unsigned char s_ok[NT];
-    __shared__ int s_nq;
-    const DecodeState *st = a.st;
-    if (st->done) return;
-    const DecodeCtx *ctx = a.ctx;
-    const int round = st->round;
-    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
-    const RoundThr th = a.thr[round];
-    const float alpha = ctx->alpha;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        s_nq = 0;
-        if (!IND) s_pe = ctx->pe;
+        S.nq = 0;
+        if (!IND) S.pe = ctx->pe;
     }
     if (LEARNED) {
         const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
-        for (int p = tid; p < RL0_MLP_PARAMS; p += NT) s_W[p] = __bfloat162float(wb[p]);
+        for (int p = tid; p < RL0_MLP_PARAMS; p += NT) S.W[p] = __bfloat162float(wb[p]);
     }
-    // (the shared copies above are first read after the candidate loop's barrier)
+    // (these shared copies are first read after a barrier of the tile body)
+}
+
+// One tile of NT columns starting at j0.  gather(row) returns (r_row, p_z(r_row)).
+template <int DMAX, bool IND, bool LEARNED, int NT, class Gather>
+__device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx, const RoundThr &th, int j0,
+                                           Gather gather, ColShared<DMAX, NT, LEARNED> &S)
+{
+    const int tid = threadIdx.x;
     const int n = a.n, d = a.d;
-    const int j = blockIdx.x * NT + tid;
+    const int j = j0 + tid;
     const bool active = j < n;
+    const float alpha = ctx->alpha;
 
     float r[DMAX];
     float nz = 0.0f, rhs = 0.0f;
@@ -193,8 +217,7 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     for (int s = 0; s < DMAX; ++s) {
         r[s] = 0.0f;
         if (s < d && active) {
-            const int row = __ldg(a.rows_sm + (size_t)s * n + j);
-            const float2 v = __ldg(rz + row);
+            const float2 v = gather(__ldg(a.rows_sm + (size_t)s * n + j));
             r[s] = v.x;
             nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
             rhs += fabsf(v.x);
@@ -204,12 +227,10 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : ctx->pe.cut, nz, need) : 0u;
     if (cand) {
 #pragma unroll
-        for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
-        s_nz[tid] = nz;
-        s_rhs[tid] = rhs;
+        for (int s = 0; s < DMAX; ++s) S.c.r[s][tid] = r[s];
+        S.c.nz[tid] = nz;
+        S.c.rhs[tid] = rhs;
     }
-    // candidates are scored by the whole CTA, one per column per pass, each
-    // column's from its highest slot down until one passes
     int best = -1;
     float bw = 0.0f;
     while (__syncthreads_or(cand != 0u)) {
@@ -217,73 +238,73 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
         if (cand) {
             ms = 31 - __clz(cand);                  // highest remaining slot first
             cand &= ~(1u << ms);
-            my = atomicAdd(&s_nq, 1);
-            s_q[my] = (unsigned short)((tid << 5) | ms);
+            my = atomicAdd(&S.nq, 1);
+            S.c.q[my] = (unsigned short)((tid << 5) | ms);
         }
         __syncthreads();
-        const int nq = s_nq;
+        const int nq = S.nq;
         if (LEARNED) {
             // the learned scorer's logit replaces n_e - n_z >= alpha: features of
             // every queued candidate, then the MLP over 32-candidate slices with
             // one thread per (candidate, hidden unit); the FMA chains are those
             // of mlp_logit, so the logits equal rl0_mlp_forward's
             for (int e = tid; e < nq; e += NT) {
-                const int owner = s_q[e] >> 5, s = s_q[e] & 31;
-                const AnchorEval E = eval_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe);
+                const int owner = S.c.q[e] >> 5, s = S.c.q[e] & 31;
+                const AnchorEval E = eval_anchor<IND>(&S.c.r[0][owner], NT, d, s, th.te, S.pe);
                 float f[RL0_NFEAT];
-                candidate_features(&s_r[0][owner], NT, d, E, s_nz[owner], s_rhs[owner], ctx->inv_sn, th.t,
+                candidate_features(&S.c.r[0][owner], NT, d, E, S.c.nz[owner], S.c.rhs[owner], ctx->inv_sn, th.t,
                                    ctx->drho, f);
 #pragma unroll
-                for (int q = 0; q < RL0_NFEAT; ++q) s_f[q][e] = f[q];
-                s_l1ok[e] = (E.lhs <= s_rhs[owner] && E.ne - s_nz[owner] >= ctx->learned_need) ? 1 : 0;
-                s_w[e] = E.w;
+                for (int q = 0; q < RL0_NFEAT; ++q) S.c.f[q][e] = f[q];
+                S.c.l1ok[e] = (E.lhs <= S.c.rhs[owner] && E.ne - S.c.nz[owner] >= ctx->learned_need) ? 1 : 0;
+                S.c.w[e] = E.w;
             }
             __syncthreads();
             for (int e0 = 0; e0 < nq; e0 += 32) {
                 for (int it = tid; it < 32 * RL0_HID; it += NT) {
                     const int el = it % 32, o = it / 32, e = e0 + el;
-                    float acc = s_W[RL0_OFF_B1 + o];
+                    float acc = S.W[RL0_OFF_B1 + o];
                     if (e < nq) {
 #pragma unroll
-                        for (int i = 0; i < RL0_NFEAT; ++i) acc = fmaf(s_f[i][e], s_W[RL0_OFF_W1 + i * RL0_HID + o], acc);
+                        for (int i = 0; i < RL0_NFEAT; ++i) acc = fmaf(S.c.f[i][e], S.W[RL0_OFF_W1 + i * RL0_HID + o], acc);
                     }
-                    s_h1[o][el] = fmaxf(acc, 0.0f);
+                    S.c.h1[o][el] = fmaxf(acc, 0.0f);
                 }
                 __syncthreads();
                 for (int it = tid; it < 32 * RL0_HID; it += NT) {
                     const int el = it % 32, o = it / 32;
-                    float acc = s_W[RL0_OFF_B2 + o];
+                    float acc = S.W[RL0_OFF_B2 + o];
 #pragma unroll 8
-                    for (int i = 0; i < RL0_HID; ++i) acc = fmaf(s_h1[i][el], s_W[RL0_OFF_W2 + i * RL0_HID + o], acc);
-                    s_h2[o][el] = fmaxf(acc, 0.0f);
+                    for (int i = 0; i < RL0_HID; ++i) acc = fmaf(S.c.h1[i][el], S.W[RL0_OFF_W2 + i * RL0_HID + o], acc);
+                    S.c.h2[o][el] = fmaxf(acc, 0.0f);
                 }
                 __syncthreads();
                 if (tid < 32 && e0 + tid < nq) {
                     const int e = e0 + tid;
-                    float out = s_W[RL0_OFF_B3];
-                    for (int o = 0; o < RL0_HID; ++o) out = fmaf(s_h2[o][tid], s_W[RL0_OFF_W3 + o], out);
-                    s_score[e] = out;
-                    s_ok[e] = (s_l1ok[e] && out >= ctx->logit_thr) ? 1 : 0;
+                    float out = S.W[RL0_OFF_B3];
+                    for (int o = 0; o < RL0_HID; ++o) out = fmaf(S.c.h2[o][tid], S.W[RL0_OFF_W3 + o], out);
+                    S.c.score[e] = out;
+                    S.c.ok[e] = (S.c.l1ok[e] && out >= ctx->logit_thr) ? 1 : 0;
                 }
                 __syncthreads();
             }
         } else {
             for (int e = tid; e < nq; e += NT) {
-                const int owner = s_q[e] >> 5, s = s_q[e] & 31;
+                const int owner = S.c.q[e] >> 5, s = S.c.q[e] & 31;
                 float sc, w;
-                s_ok[e] = score_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, s_pe, s_nz[owner], s_rhs[owner], alpha,
-                                            &sc, &w) ? 1 : 0;
-                s_score[e] = sc;
-                s_w[e] = w;
+                S.c.ok[e] = score_anchor<IND>(&S.c.r[0][owner], NT, d, s, th.te, S.pe, S.c.nz[owner], S.c.rhs[owner],
+                                              alpha, &sc, &w) ? 1 : 0;
+                S.c.score[e] = sc;
+                S.c.w[e] = w;
             }
         }
         __syncthreads();
-        if (my >= 0 && s_ok[my]) {                  // the first pass from the top is the last passing
+        if (my >= 0 && S.c.ok[my]) {                // the first pass from the top is the last passing
             best = ms;                              // anchor in row order: it stands, the rest is moot
-            bw = s_w[my];
+            bw = S.c.w[my];
             cand = 0u;
         }
-        if (tid == 0) s_nq = 0;
+        if (tid == 0) S.nq = 0;
     }
     const bool pass = best >= 0;
     float old = 0.0f, nv = 0.0f;
@@ -322,22 +343,76 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
             if (fresh) a.list[base + __popc(mask & ((1u << lane) - 1u))] = j;
         }
     }
-    // ---- the launch's last CTA applies H_k when |supp x'| > k (state read past L1)
-    __shared__ HkShared s_hk;
-    __shared__ unsigned s_suf[NT];
-    __shared__ int s_last;
+}
+
+// The launch's last CTA applies H_k when |supp x'| > k (state read past L1,
+// since other CTAs updated it during this launch).
+template <int DMAX, int NT, bool LEARNED>
+__device__ __forceinline__ void col_last_cta(const KArgs &a, const DecodeCtx *ctx, ColShared<DMAX, NT, LEARNED> &S)
+{
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&a.st->col_done, 1u) == gridDim.x - 1u);
+    if (threadIdx.x == 0) S.last = (atomicAdd(&a.st->col_done, 1u) == gridDim.x - 1u);
     __syncthreads();
-    if (!s_last) return;
+    if (!S.last) return;
     __threadfence();
     DecodeState *stw = a.st;
     const unsigned upd = __ldcg(&stw->upd_count);
     const long long nnz = (long long)__ldcg(&stw->nnz) + __ldcg(&stw->nnz_delta);
-    if (tid == 0) stw->col_done = 0u;
+    if (threadIdx.x == 0) stw->col_done = 0u;
     if (upd == 0 || nnz <= ctx->k) return;
-    cta_hk_select<NT>(a.list, __ldcg(&stw->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &stw->drop_count, s_hk, s_suf);
+    cta_hk_select<NT>(a.list, __ldcg(&stw->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &stw->drop_count, S.h.hk,
+                      S.h.suf);
+}
+
+template <int DMAX, bool IND, bool LEARNED>
+__global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
+{
+    constexpr int NT = ColBlock<DMAX>::value;
+    __shared__ ColShared<DMAX, NT, LEARNED> S;
+    const DecodeState *st = a.st;
+    if (st->done) return;
+    const DecodeCtx *ctx = a.ctx;
+    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
+    const RoundThr th = a.thr[st->round];
+    col_setup<DMAX, IND, LEARNED, NT>(ctx, S);
+    score_tile<DMAX, IND, LEARNED, NT>(a, ctx, th, blockIdx.x * NT, [rz](int row) { return __ldg(rz + row); }, S);
+    col_last_cta<DMAX, NT, LEARNED>(a, ctx, S);
+}
+
+// Cluster variant: CTA `rank` of each cluster stages rows [rank << sh,
+// (rank + 1) << sh) of r_hat in shared memory; every gather reads the owning
+// CTA's slice through the cluster's shared window.  CTAs loop over tiles; the
+// cluster barriers (hardware, no spinning) keep each slice alive until every
+// CTA of the cluster is done with it.
+template <int DMAX, bool IND>
+__global__ void __launch_bounds__(RL0_DSM_NT) k_column_score_dsm(KArgs a, int sh, int ntiles)
+{
+    constexpr int NT = RL0_DSM_NT;
+    extern __shared__ __align__(16) unsigned char s_dyn[];     // [slice of r_hat | ColShared]
+    float2 *s_slice = reinterpret_cast<float2 *>(s_dyn);
+    ColShared<DMAX, NT, false> &S = *reinterpret_cast<ColShared<DMAX, NT, false> *>(s_dyn + (sizeof(float2) << sh));
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const DecodeState *st = a.st;
+    if (st->done) return;                                  // uniform over the grid
+    const DecodeCtx *ctx = a.ctx;
+    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
+    const int rank = (int)cl.block_rank();
+    const int r0 = rank << sh, r1 = min(r0 + (1 << sh), a.m);
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) s_slice[i - r0] = __ldg(rz + i);
+    col_setup<DMAX, IND, false, NT>(ctx, S);
+    const RoundThr th = a.thr[st->round];
+    cl.sync();
+    const int msk = (1 << sh) - 1;
+    auto gather = [&](int row) -> float2 {
+        const float2 *p = cl.map_shared_rank(s_slice, (unsigned)(row >> sh));
+        return p[row & msk];
+    };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        score_tile<DMAX, IND, false, NT>(a, ctx, th, tile * NT, gather, S);
+    cl.sync();
+    col_last_cta<DMAX, NT, false>(a, ctx, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,6 +723,8 @@ struct GraphCache {
     cudaStream_t capture_stream = nullptr;
 };
 
+template <bool IND> void plan_dsm_one(KArgs &a);
+
 KArgs make_args(const rl0_expander *A)
 {
     const Workspace &w = A->ws;
@@ -678,11 +755,76 @@ KArgs make_args(const rl0_expander *A)
     a.thr = w.thr;
     a.rlog = w.rlog;
     a.final_part = w.final_part;
+    if (A->d <= 8) {
+        KArgs b = a;
+        plan_dsm_one<true>(b);
+        plan_dsm_one<false>(a);
+        if (b.dsm_grid != a.dsm_grid || b.dsm_sh != a.dsm_sh) a.dsm_grid = 0;   // one plan for both kinds
+    }
     return a;
+}
+
+template <bool IND>
+cudaError_t launch_dsm(const KArgs &a, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(a.dsm_grid);
+    cfg.blockDim = dim3(RL0_DSM_NT);
+    cfg.dynamicSmemBytes = (sizeof(float2) << a.dsm_sh) + sizeof(ColShared<8, RL0_DSM_NT, false>);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.dsm_cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int ntiles = (int)rl0_div_up(a.n, RL0_DSM_NT);
+    return cudaLaunchKernelEx(&cfg, k_column_score_dsm<8, IND>, a, a.dsm_sh, ntiles);
+}
+
+// Cluster schedule of the column kernel for an expander: the smallest slice
+// 2^sh >= 1024 rows with at most 8 slices covering m, and as many clusters as
+// fit at once.  Returns 0 (cluster kernel off) when m needs more than 8 x 16384
+// rows or no cluster fits.
+template <bool IND>
+void plan_dsm_one(KArgs &a)
+{
+    int sh = 10;
+    while (sh < 14 && ((long long)a.m + (1LL << sh) - 1) / (1LL << sh) > 8) ++sh;
+    const int C = (int)(((long long)a.m + (1LL << sh) - 1) >> sh);
+    if (C > 8 || C < 1) return;
+    const size_t dyn = (sizeof(float2) << sh) + sizeof(ColShared<8, RL0_DSM_NT, false>);
+    if (cudaFuncSetAttribute((const void *)k_column_score_dsm<8, IND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn) != cudaSuccess) { cudaGetLastError(); return; }
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(RL0_DSM_NT);
+    cfg.dynamicSmemBytes = dyn;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_column_score_dsm<8, IND>, &cfg) != cudaSuccess ||
+        nclusters < 1) { cudaGetLastError(); return; }
+    a.dsm_sh = sh;
+    a.dsm_cluster = C;
+    a.dsm_grid = nclusters * C;
 }
 
 void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
+    if (!learned && dmax == 8 && a.dsm_grid > 0) {
+        if (indicator) launch_dsm<true>(a, s);
+        else launch_dsm<false>(a, s);
+        return;
+    }
 #define RL0_CS(D, I, L) k_column_score<D, I, L><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
     if (learned) {
         if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }
