@@ -42,6 +42,7 @@ struct BatchItem {
     float alpha;
     double stop_level, stop_rel;
     Series pz, pe;
+    float pe_b1, pe_c1;                             // fast-path bound of q_e (see anchor_candidates)
     const RoundThr *thr;
     const int32_t *rows_sm, *rows_cm, *rowptr, *colidx;
     const float *y;
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                         rhs += fabsf(v.x);
                     }
                 }
-                unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, nz, IND ? alpha : alpha - 1e-3f)
+                unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, I.pe_b1,
+                                                                      I.pe_c1, nz, IND ? alpha : alpha - 1e-3f)
                                        : 0u;
                 if (cand) {
 #pragma unroll
@@ -529,6 +531,8 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
         It.stop_rel = ctx[i].stop_rel;
         It.pz = ctx[i].pz;
         It.pe = ctx[i].pe;
+        It.pe_b1 = ctx[i].pe_b1;
+        It.pe_c1 = ctx[i].pe_c1;
         It.thr = B.d_thr + thr_off[i];
         It.rows_sm = X->rows_sm;
         It.rows_cm = X->rows_cm;

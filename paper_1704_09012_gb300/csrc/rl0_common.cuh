@@ -103,6 +103,7 @@ struct DecodeCtx {
     float learned_need;       // learned: candidates need n_e - n_z bound >= this
     float inv_sn;             // 1 / sigma_n (0 when noiseless)
     float drho;               // d k / m
+    float pe_b1, pe_c1;       // q_e(D) <= 1 / (1 + c1 (u + u^2/2)), u = b1 D^2 (fast-path bound)
     int32_t *passed;          // optional per-column pass flags (round_step)
     int want_log;
     int no_accept;            // round_step: stop after the rebuild (no accept, no undo)

@@ -28,7 +28,6 @@
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
 #include <cuda_bf16.h>
-#include <cooperative_groups.h>
 
 #define CK(call)                                          \
     do {                                                  \
@@ -53,7 +52,6 @@ struct KArgs {
     double *final_part;
     cudaGraphConditionalHandle cond;   // while-loop condition of the round graph
     int has_cond;
-    int dsm_sh, dsm_cluster, dsm_grid; // cluster column kernel: slice 2^sh rows, CTAs per cluster, grid (0: off)
 };
 
 // r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
@@ -149,14 +147,8 @@ __global__ void k_list_count_from_support(KArgs a)
 // n_e, omega and l1 test from residuals kept in shared memory, scored by the
 // whole CTA from each column's highest slot down until one passes (that one is
 // the last passing anchor in row order, whose omega the column takes).
-//
-// Two kernels share the tile body: k_column_score gathers (r_i, p_z(r_i))
-// from L2; k_column_score_dsm stages r_hat in the distributed shared memory of
-// a thread-block cluster (each CTA holds a 2^slice_shift-row slice) and
-// gathers with cluster-shared loads.
 // ---------------------------------------------------------------------------
 template <int DMAX> struct ColBlock { static constexpr int value = DMAX <= 8 ? 256 : (DMAX <= 16 ? 128 : 64); };
-#define RL0_DSM_NT 1024
 
 // Shared memory of the column kernels.  H_k's scratch (used by the launch's
 // last CTA after its tiles) shares the bytes of the candidate queue.
@@ -224,7 +216,8 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
         }
     }
     const float need = LEARNED ? (IND ? ctx->learned_need : ctx->learned_need - 1e-3f) : (IND ? alpha : alpha - 1e-3f);
-    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : ctx->pe.cut, nz, need) : 0u;
+    unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : ctx->pe.cut, ctx->pe_b1,
+                                                          ctx->pe_c1, nz, need) : 0u;
     if (cand) {
 #pragma unroll
         for (int s = 0; s < DMAX; ++s) S.c.r[s][tid] = r[s];
@@ -378,41 +371,6 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     col_setup<DMAX, IND, LEARNED, NT>(ctx, S);
     score_tile<DMAX, IND, LEARNED, NT>(a, ctx, th, blockIdx.x * NT, [rz](int row) { return __ldg(rz + row); }, S);
     col_last_cta<DMAX, NT, LEARNED>(a, ctx, S);
-}
-
-// Cluster variant: CTA `rank` of each cluster stages rows [rank << sh,
-// (rank + 1) << sh) of r_hat in shared memory; every gather reads the owning
-// CTA's slice through the cluster's shared window.  CTAs loop over tiles; the
-// cluster barriers (hardware, no spinning) keep each slice alive until every
-// CTA of the cluster is done with it.
-template <int DMAX, bool IND>
-__global__ void __launch_bounds__(RL0_DSM_NT) k_column_score_dsm(KArgs a, int sh, int ntiles)
-{
-    constexpr int NT = RL0_DSM_NT;
-    extern __shared__ __align__(16) unsigned char s_dyn[];     // [slice of r_hat | ColShared]
-    float2 *s_slice = reinterpret_cast<float2 *>(s_dyn);
-    ColShared<DMAX, NT, false> &S = *reinterpret_cast<ColShared<DMAX, NT, false> *>(s_dyn + (sizeof(float2) << sh));
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const DecodeState *st = a.st;
-    if (st->done) return;                                  // uniform over the grid
-    const DecodeCtx *ctx = a.ctx;
-    const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
-    const int rank = (int)cl.block_rank();
-    const int r0 = rank << sh, r1 = min(r0 + (1 << sh), a.m);
-    for (int i = r0 + (int)threadIdx.x; i < r1; i += NT) s_slice[i - r0] = __ldg(rz + i);
-    col_setup<DMAX, IND, false, NT>(ctx, S);
-    const RoundThr th = a.thr[st->round];
-    cl.sync();
-    const int msk = (1 << sh) - 1;
-    auto gather = [&](int row) -> float2 {
-        const float2 *p = cl.map_shared_rank(s_slice, (unsigned)(row >> sh));
-        return p[row & msk];
-    };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        score_tile<DMAX, IND, false, NT>(a, ctx, th, tile * NT, gather, S);
-    cl.sync();
-    col_last_cta<DMAX, NT, false>(a, ctx, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -672,7 +630,7 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_collect(KArgs a, floa
         }
     }
     const float need = IND ? ctx->learned_need : ctx->learned_need - 1e-3f;
-    unsigned cand = anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, nz, need);
+    unsigned cand = anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, ctx->pe_b1, ctx->pe_c1, nz, need);
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
     for (; cand; cand &= cand - 1u) {
@@ -723,8 +681,6 @@ struct GraphCache {
     cudaStream_t capture_stream = nullptr;
 };
 
-template <bool IND> void plan_dsm_one(KArgs &a);
-
 KArgs make_args(const rl0_expander *A)
 {
     const Workspace &w = A->ws;
@@ -755,76 +711,11 @@ KArgs make_args(const rl0_expander *A)
     a.thr = w.thr;
     a.rlog = w.rlog;
     a.final_part = w.final_part;
-    if (A->d <= 8) {
-        KArgs b = a;
-        plan_dsm_one<true>(b);
-        plan_dsm_one<false>(a);
-        if (b.dsm_grid != a.dsm_grid || b.dsm_sh != a.dsm_sh) a.dsm_grid = 0;   // one plan for both kinds
-    }
     return a;
-}
-
-template <bool IND>
-cudaError_t launch_dsm(const KArgs &a, cudaStream_t s)
-{
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(a.dsm_grid);
-    cfg.blockDim = dim3(RL0_DSM_NT);
-    cfg.dynamicSmemBytes = (sizeof(float2) << a.dsm_sh) + sizeof(ColShared<8, RL0_DSM_NT, false>);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = a.dsm_cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const int ntiles = (int)rl0_div_up(a.n, RL0_DSM_NT);
-    return cudaLaunchKernelEx(&cfg, k_column_score_dsm<8, IND>, a, a.dsm_sh, ntiles);
-}
-
-// Cluster schedule of the column kernel for an expander: the smallest slice
-// 2^sh >= 1024 rows with at most 8 slices covering m, and as many clusters as
-// fit at once.  Returns 0 (cluster kernel off) when m needs more than 8 x 16384
-// rows or no cluster fits.
-template <bool IND>
-void plan_dsm_one(KArgs &a)
-{
-    int sh = 10;
-    while (sh < 14 && ((long long)a.m + (1LL << sh) - 1) / (1LL << sh) > 8) ++sh;
-    const int C = (int)(((long long)a.m + (1LL << sh) - 1) >> sh);
-    if (C > 8 || C < 1) return;
-    const size_t dyn = (sizeof(float2) << sh) + sizeof(ColShared<8, RL0_DSM_NT, false>);
-    if (cudaFuncSetAttribute((const void *)k_column_score_dsm<8, IND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dyn) != cudaSuccess) { cudaGetLastError(); return; }
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(RL0_DSM_NT);
-    cfg.dynamicSmemBytes = dyn;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_column_score_dsm<8, IND>, &cfg) != cudaSuccess ||
-        nclusters < 1) { cudaGetLastError(); return; }
-    a.dsm_sh = sh;
-    a.dsm_cluster = C;
-    a.dsm_grid = nclusters * C;
 }
 
 void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-    if (!learned && dmax == 8 && a.dsm_grid > 0) {
-        if (indicator) launch_dsm<true>(a, s);
-        else launch_dsm<false>(a, s);
-        return;
-    }
 #define RL0_CS(D, I, L) k_column_score<D, I, L><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
     if (learned) {
         if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }

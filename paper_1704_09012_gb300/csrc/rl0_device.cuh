@@ -191,36 +191,47 @@ __device__ __forceinline__ float mlp_logit(const float *W, const float *f)
 }
 
 // Fast-path bound of Alg. 2's test for every anchor of a column held in
-// registers: the anchors (|r_i| >= ta) whose n_e can still reach n_z + need,
-// with n_e <= 1 + #{l != i : |r_i - r_l| <= reach}.  Callers pass
-// need = alpha for the 0/1 scores (exact counts) and alpha - 1e-3 for the
-// continuous ones (FP32 sums of values <= 1).
+// registers: the anchors (|r_i| >= ta) whose n_e can still reach n_z + need.
+//  - 0/1 scores: n_e = 1 + #{l != i : |r_i - r_l| <= te} exactly;
+//  - continuous scores: q_e(D) = 0 beyond the cut (reach) and otherwise
+//    q_e(D) <= 1 / (1 + c1 (u + u^2/2)), u = b1 D^2 (b1 the smallest b_q of the
+//    q >= 1 terms, c1 = 1 - a_0), so n_e <= 1 + the sum of these bounds.
+// Callers pass need = alpha for the 0/1 scores and alpha - 1e-3 for the
+// continuous ones (the slack covers FP32 rounding in the bound and in n_e).
 template <int DMAX, bool IND>
-__device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, float ta, float reach, float nz,
-                                                      float need)
+__device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, float ta, float reach, float b1,
+                                                      float c1, float nz, float need)
 {
     unsigned amask = 0;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)
         if (s < d && fabsf(r[s]) >= ta) amask |= 1u << s;
     if (!amask) return 0u;
-    unsigned nm[DMAX];
+    float ub[DMAX];
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) nm[s] = 0u;
+    for (int s = 0; s < DMAX; ++s) ub[s] = 1.0f;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
 #pragma unroll
         for (int l = s + 1; l < DMAX; ++l) {
-            if (l < d && fabsf(r[s] - r[l]) <= reach) {
-                nm[s] |= 1u << l;
-                nm[l] |= 1u << s;
+            if (l < d) {
+                const float D = r[s] - r[l];
+                if (fabsf(D) <= reach) {
+                    float q = 1.0f;
+                    if (!IND) {
+                        const float u = b1 * (D * D);
+                        q = __frcp_rn(fmaf(c1, fmaf(0.5f * u, u, u), 1.0f));
+                    }
+                    ub[s] += q;
+                    ub[l] += q;
+                }
             }
         }
     }
     unsigned cand = 0;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)
-        if (((amask >> s) & 1u) && (1.0f + (float)__popc(nm[s])) - nz >= need) cand |= 1u << s;
+        if (((amask >> s) & 1u) && ub[s] - nz >= need) cand |= 1u << s;
     return cand;
 }
 

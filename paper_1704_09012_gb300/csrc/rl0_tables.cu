@@ -275,6 +275,12 @@ void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx,
         he = make_series(2.0 * d * rho, s2, 2.0 * n2, p.ell);
         ctx->pz = to_device_series(hz);
         ctx->pe = to_device_series(he);
+        // every q >= 1 term has b_q >= b_1 and e^x >= 1 + x + x^2/2, so
+        // p_e(D) = 1/F_e(D) <= 1 / (1 + (1 - a_0)(u + u^2/2)), u = b_1 D^2
+        double bmin = INFINITY;
+        for (int q = 1; q < he.nq; ++q) bmin = std::fmin(bmin, he.b[q]);
+        ctx->pe_b1 = (float)bmin;
+        ctx->pe_c1 = (float)(1.0 - he.a[0]);
     }
     for (int r = 0; r < nthr; ++r) {
         const double t = 1.0 - r * p.c;
