@@ -1,0 +1,397 @@
+// rl0_column_res.cu -- the column score of Robust-l0 (arXiv 1704.09012,
+// Algorithm 2, the loop over j in [n] and i in N(j)) with every row's
+// residual code resident in shared memory.
+//
+// One CTA per SM; CTA b owns the contiguous columns [b n / G, (b + 1) n / G).
+//   load     the CTA copies the 16-bit codes of all m rows (and the p_z bound
+//            table) into shared memory with bulk asynchronous copies
+//            (cp.async.bulk + mbarrier), 2 bytes per row;
+//   stream   each thread takes one column per tile of NT columns, reads its d
+//            row ids from HBM (one coalesced 4-byte load per slot; the next
+//            tile's are prefetched) and its d codes from shared memory, and
+//            bounds the column's anchors with code_candidates; no thread
+//            waits on another, and the few columns that survive go on the
+//            CTA's slice [lo, hi) of a list in global memory;
+//   resolve  with the codes no longer needed, their shared memory stages the
+//            survivors, NT at a time: one thread per column reads its FP32
+//            (r, p_z) and applies anchor_candidates, one thread per candidate
+//            (column, slot) scores it, and each column takes its highest
+//            passing slot (the last passing anchor in row order); the CTA
+//            then commits with one global atomic per counter;
+//   H_k      the launch's last CTA applies H_k, its scratch in the bytes that
+//            held the codes.
+// The resolve runs the arithmetic of k_column_score in the same order, so
+// both kernels give the same x'.
+#include <algorithm>
+
+#include "rl0_common.cuh"
+#include "rl0_device.cuh"
+#include "rl0_round.cuh"
+
+#define RL0_RES_CHUNK 32768u            // bytes per bulk copy
+#define RL0_RES_WAIT_LIMIT (1u << 22)   // try_wait polls before a copy counts as lost
+#define RL0_RES_MAX_NT 1024
+
+namespace {
+
+struct ResShared {
+    Series pe;
+    unsigned long long bar;             // completion of the bulk copies
+    int count, last;
+    unsigned total, ubase, fbase;
+};
+
+// Bytes of the code region, which later holds the resolve scratch and, in
+// the last CTA, H_k's scratch.
+unsigned res_region_bytes(long long m, int nt, size_t scratch)
+{
+    const size_t codes = 2 * (size_t)rl0_code_rows(m);
+    const size_t hk = ((sizeof(HkShared) + 15) & ~(size_t)15) + 4 * (size_t)nt;
+    return (unsigned)((std::max(std::max(codes, hk), scratch) + 15) & ~(size_t)15);
+}
+
+__device__ __forceinline__ bool mbar_try_wait_bounded(unsigned bar, unsigned parity)
+{
+    for (unsigned it = 0; it < RL0_RES_WAIT_LIMIT; ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Resolve scratch, laid over the code region once the stream is done: a
+// batch of NT listed columns and their candidate items (at most DMAX each).
+template <int DMAX, int NT>
+struct ResScratch {
+    float r[DMAX][NT];                   // FP32 residuals of the batch's columns
+    float nz[NT], rhs[NT];
+    unsigned off[NT];                    // first item of each column
+    unsigned short it_e[NT * DMAX];      // item -> column in the batch
+    unsigned char it_s[NT * DMAX];       // item -> slot (descending within a column)
+    unsigned char it_ok[NT * DMAX];
+    float it_w[NT * DMAX];
+    unsigned wsum[NT / 32];
+};
+
+// Exclusive prefix over the CTA of v (NT threads, all of them call it);
+// *total (shared) gets the sum.  wsum: NT / 32 shared words.
+template <int NT>
+__device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsum, unsigned *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned w = (lane < NT / 32) ? wsum[lane] : 0u;
+        unsigned wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < NT / 32) wsum[lane] = wi - w;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    const unsigned r = wsum[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// DMAX slots per column; EXACT: d == DMAX (the slot guards fold away).
+template <int DMAX, bool IND, bool EXACT, int NT>
+__global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DecodeState *st = a.st;
+    if (st->done) return;
+    const DecodeCtx *ctx = a.ctx;
+    const int n = a.n, tid = threadIdx.x;
+    const int d = EXACT ? DMAX : a.d;
+    const unsigned short *s_code = (const unsigned short *)dsm;
+    const float *s_pz = (const float *)(dsm + a.res_pz_off);
+    ResShared &S = *(ResShared *)(dsm + a.res_s_off);
+    const int cur = st->cur;
+    const float2 *__restrict__ rz = cur ? a.rz1 : a.rz0;
+    const RoundThr th = a.thr[st->round];
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&S.bar);
+    if (tid == 0) {
+        S.count = 0;
+        if (!IND) S.pe = ctx->pe;
+        const unsigned code_bytes = 2u * (unsigned)rl0_code_rows(a.m);
+        const unsigned bytes = code_bytes + (IND ? 0u : 4u * RL0_PZ_BINS);
+        const unsigned char *src = (const unsigned char *)(cur ? a.code1 : a.code0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(dsm);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (((dst | (unsigned)(size_t)src | (unsigned)(size_t)a.pzlb) & 15u) != 0u) {
+            // bulk copies need 16-byte alignment: report it, complete the phase, copy nothing
+            atomicExch(&st->status, (int)RL0_ERR_CUDA);
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+        } else {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+            for (unsigned o = 0; o < code_bytes; o += RL0_RES_CHUNK) {
+                const unsigned sz = (code_bytes - o < RL0_RES_CHUNK) ? code_bytes - o : RL0_RES_CHUNK;
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(dst + o), "l"(src + o), "r"(sz), "r"(bar) : "memory");
+            }
+            if (!IND)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(dst + a.res_pz_off), "l"(a.pzlb), "r"(4u * RL0_PZ_BINS), "r"(bar) : "memory");
+        }
+    }
+    // this CTA's columns: [lo, hi), equal shares of n
+    const int lo = (int)(((long long)blockIdx.x * n) / gridDim.x);
+    const int hi = (int)(((long long)(blockIdx.x + 1) * n) / gridDim.x);
+    int j0 = lo;
+    int nxt[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        const int j = j0 + tid;
+        nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+    }
+    __syncthreads();                               // the barrier is initialised
+    const bool arrived = mbar_try_wait_bounded(bar, 0u);
+    if (__syncthreads_or(!arrived || __ldcg(&st->status) == (int)RL0_ERR_CUDA)) {
+        // a copy did not complete in time: record it, give the copies one more
+        // bounded wait, skip the columns (the last-CTA count below still runs)
+        if (tid == 0 && !arrived) {
+            atomicCAS(&st->status, 0, (int)RL0_ERR_TIMEOUT);
+            mbar_try_wait_bounded(bar, 0u);
+        }
+        j0 = hi;
+    }
+    const CodeThr ct = code_thresholds(th.ta, th.tz, IND ? th.te : S.pe.cut);
+    const float b1 = ctx->pe_b1, c1 = ctx->pe_c1;
+    const float need = IND ? ctx->alpha : ctx->alpha - 1e-3f;
+    int32_t *passed = ctx->passed;
+    const int lane = tid & 31;
+    int *seg = a.res_list + lo;                    // this CTA's slice of the survivor list
+    for (; j0 < hi; j0 += NT) {
+        int rid[DMAX];
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) rid[s] = nxt[s];
+        {
+            const int jn = j0 + NT + tid;
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (s < d && jn < hi) nxt[s] = __ldg(a.rows_sm + (size_t)s * n + jn);
+        }
+        const int j = j0 + tid;
+        const bool active = j < hi;
+        const bool cand =
+            active && code_candidates<DMAX, IND>(s_code, s_pz, rid, d, ct, b1, c1, need) != 0u;
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&S.count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (cand && pos < hi - lo) seg[pos] = j;   // pos < hi - lo always: one entry per column
+        }
+        if (passed && active && !cand) passed[j] = 0;
+    }
+    __syncthreads();                               // the stream is done: the codes' bytes become scratch
+    const int count = min(S.count, hi - lo);
+    ResScratch<DMAX, NT> &R = *(ResScratch<DMAX, NT> *)dsm;
+    const float alpha = ctx->alpha;
+    const float reach = IND ? th.te : S.pe.cut;
+    for (int b0 = 0; b0 < count; b0 += NT) {
+        // one thread per listed column: FP32 residuals, exact candidates
+        const int e = b0 + tid;
+        const bool act = e < count;
+        const int j = act ? __ldcg(seg + e) : 0;
+        unsigned cand = 0u;
+        if (act) {
+            int rid[DMAX];
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) rid[s] = (s < d) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+            float r[DMAX];
+            float nz = 0.0f, rhs = 0.0f;
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) {
+                r[s] = 0.0f;
+                if (s < d) {
+                    const float2 v = __ldg(rz + rid[s]);
+                    r[s] = v.x;
+                    nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
+                    rhs += fabsf(v.x);
+                }
+                R.r[s][tid] = r[s];
+            }
+            R.nz[tid] = nz;
+            R.rhs[tid] = rhs;
+            cand = anchor_candidates<DMAX, IND>(r, d, th.ta, reach, b1, c1, nz, need);
+        }
+        // one item per candidate (column, slot), a column's slots in descending order
+        const unsigned nc = (unsigned)__popc(cand);
+        const unsigned off = cta_exclusive_scan<NT>(nc, R.wsum, &S.total);
+        const unsigned nitems = S.total;
+        {
+            unsigned c = cand, q = off;
+            while (c) {
+                const int sl = 31 - __clz(c);
+                c &= ~(1u << sl);
+                R.it_e[q] = (unsigned short)tid;
+                R.it_s[q] = (unsigned char)sl;
+                ++q;
+            }
+        }
+        __syncthreads();
+        for (unsigned k = tid; k < nitems; k += NT) {
+            const int ee = R.it_e[k], sl = R.it_s[k];
+            const AnchorEval E = eval_anchor<IND>(&R.r[0][ee], NT, d, sl, th.te, S.pe);
+            R.it_ok[k] = (E.lhs <= R.rhs[ee] && E.ne - R.nz[ee] >= alpha) ? 1 : 0;
+            R.it_w[k] = E.w;
+        }
+        __syncthreads();
+        // each column: its first passing item is its highest passing slot
+        int best = -1;
+        float bw = 0.0f;
+        for (unsigned q = 0; q < nc; ++q)
+            if (R.it_ok[off + q]) {
+                best = R.it_s[off + q];
+                bw = R.it_w[off + q];
+                break;
+            }
+        const bool pass = best >= 0;
+        float old = 0.0f, nv = 0.0f;
+        if (pass) {
+            old = ctx->x[j];
+            nv = old + bw;
+            ctx->x[j] = nv;
+        }
+        if (passed && act) passed[j] = pass ? 1 : 0;
+        // the batch's commit: one global atomic per counter
+        const bool fresh = pass && old == 0.0f && nv != 0.0f;
+        const unsigned pf = cta_exclusive_scan<NT>((pass ? 0x10000u : 0u) | (fresh ? 1u : 0u), R.wsum, &S.total);
+        const unsigned tpf = S.total;
+        const int ngone = __syncthreads_count(pass && old != 0.0f && nv == 0.0f);
+        const int nup = __syncthreads_count(pass && old == 0.0f && nv != 0.0f);
+        const int ndown = __syncthreads_count(pass && old != 0.0f && nv == 0.0f);
+        if (tid == 0) {
+            if (nup != ndown) atomicAdd(&st->nnz_delta, nup - ndown);
+            if (ngone) atomicAdd(&st->zeroed, (unsigned)ngone);
+            S.ubase = (tpf >> 16) ? atomicAdd(&st->upd_count, tpf >> 16) : 0u;
+            S.fbase = (tpf & 0xffffu) ? atomicAdd(&st->list_count, tpf & 0xffffu) : 0u;
+        }
+        __syncthreads();
+        if (pass) {
+            UndoEntry u;
+            u.j = j;
+            u.old = old;
+            a.ulog[S.ubase + (pf >> 16)] = u;
+        }
+        if (fresh) a.list[S.fbase + (pf & 0xffffu)] = j;
+        __syncthreads();                           // the scratch is reused by the next batch
+    }
+    // the codes are no longer needed: their bytes become H_k's scratch
+    HkShared &hk = *(HkShared *)dsm;
+    unsigned *suf = (unsigned *)(dsm + ((sizeof(HkShared) + 15) & ~(size_t)15));
+    last_cta_hk<NT>(a, ctx, hk, suf, &S.last);
+}
+
+// Threads per CTA of each variant (the exact d <= 7 variants fit 64 registers).
+template <int DMAX, bool EXACT> struct ResNT {
+    static constexpr int value = (EXACT && DMAX <= 7) ? 1024 : (DMAX <= 16 ? 512 : 256);
+};
+
+template <int DMAX, bool EXACT>
+bool res_attr(unsigned smem)
+{
+    constexpr int NT = ResNT<DMAX, EXACT>::value;
+    if (cudaFuncSetAttribute(k_column_score_res<DMAX, false, EXACT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_column_score_res<DMAX, true, EXACT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Variant for column degree d: exact for 6 <= d <= 8, else the smallest DMAX >= d.
+int res_variant(int d) { return (d >= 6 && d <= 8) ? d : (d < 6 ? 8 : (d <= 16 ? 16 : 32)); }
+size_t res_scratch_bytes(int d)
+{
+    switch (res_variant(d)) {
+    case 6: return sizeof(ResScratch<6, ResNT<6, true>::value>);
+    case 7: return sizeof(ResScratch<7, ResNT<7, true>::value>);
+    case 8: return d == 8 ? sizeof(ResScratch<8, ResNT<8, true>::value>) : sizeof(ResScratch<8, ResNT<8, false>::value>);
+    case 16: return sizeof(ResScratch<16, ResNT<16, false>::value>);
+    default: return sizeof(ResScratch<32, ResNT<32, false>::value>);
+    }
+}
+
+int res_nt(int d)
+{
+    switch (res_variant(d)) {
+    case 6: return ResNT<6, true>::value;
+    case 7: return ResNT<7, true>::value;
+    case 8: return d == 8 ? ResNT<8, true>::value : ResNT<8, false>::value;
+    case 16: return ResNT<16, false>::value;
+    default: return ResNT<32, false>::value;
+    }
+}
+
+}  // namespace
+
+void rl0_res_setup(const rl0_expander *A, KArgs *a)
+{
+    a->res_ok = 0;
+    if (!A->ws.code[0] || !A->ws.code[1] || !A->ws.pzlb || !A->ws.res_list) return;
+    const int nt = res_nt(A->d);
+    const unsigned region = res_region_bytes(A->m, nt, res_scratch_bytes(A->d));
+    a->res_pz_off = region;
+    a->res_s_off = region + 4u * RL0_PZ_BINS;
+    a->res_smem = a->res_s_off + (unsigned)sizeof(ResShared);
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, A->device) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (a->res_smem > (unsigned)optin) return;
+    bool ok = false;
+    switch (res_variant(A->d)) {
+    case 6: ok = res_attr<6, true>(a->res_smem); break;
+    case 7: ok = res_attr<7, true>(a->res_smem); break;
+    case 8: ok = (A->d == 8) ? res_attr<8, true>(a->res_smem) : res_attr<8, false>(a->res_smem); break;
+    case 16: ok = res_attr<16, false>(a->res_smem); break;
+    default: ok = res_attr<32, false>(a->res_smem); break;
+    }
+    if (!ok) return;
+    const long long ntiles = rl0_div_up(A->n, nt);
+    a->res_grid = (int)(ntiles < a->nsm ? ntiles : a->nsm);
+    a->res_ok = 1;
+}
+
+bool rl0_res_launch(const KArgs &a, int indicator, cudaStream_t s)
+{
+    if (!a.res_ok) return false;
+#define RL0_CR(D, E) do {                                                                                   \
+        constexpr int NT_ = ResNT<D, E>::value;                                                              \
+        if (indicator) k_column_score_res<D, true, E, NT_><<<a.res_grid, NT_, a.res_smem, s>>>(a);         \
+        else k_column_score_res<D, false, E, NT_><<<a.res_grid, NT_, a.res_smem, s>>>(a);                  \
+    } while (0)
+    switch (res_variant(a.d)) {
+    case 6: RL0_CR(6, true); break;
+    case 7: RL0_CR(7, true); break;
+    case 8: if (a.d == 8) RL0_CR(8, true); else RL0_CR(8, false); break;
+    case 16: RL0_CR(16, false); break;
+    default: RL0_CR(32, false); break;
+    }
+#undef RL0_CR
+    return true;
+}

@@ -12,6 +12,12 @@
 #define RL0_ROWS_CHUNK 256   // rows per l1 partial, one row per thread (fixed: defines the summation order)
 #define RL0_MAX_D 32
 
+// 16-bit residual codes read by the column kernel's bound (rl0_device.cuh):
+// r rounded toward zero to FP16, magnitude clamped to the largest finite code.
+// The p_z lower-bound table has one entry per 2^RL0_PZ_SHIFT magnitude codes.
+#define RL0_PZ_SHIFT 5
+#define RL0_PZ_BINS (0x7c00 >> RL0_PZ_SHIFT)
+
 // Status codes a kernel can leave in DecodeState::status.
 #define RL0_DEV_OK 0
 #define RL0_DEV_TIMEOUT 1
@@ -117,6 +123,9 @@ struct UndoEntry {
 // Device workspace owned by an expander.
 struct Workspace {
     float2 *rz[2];            // (r_i, p_z(r_i)) for r_hat and the candidate r
+    unsigned short *code[2];  // 16-bit codes of the same residuals, padded to a multiple of 8 rows
+    float *pzlb;              // p_z lower bound per code bin, float[RL0_PZ_BINS]
+    int *res_list;            // survivors of the column kernel's code bound, int[n]
     int *list;                // support + new nonzeros, capacity n
     int *list_tmp;            // compaction scratch, capacity n
     UndoEntry *ulog;          // updates of this round, capacity n
@@ -178,6 +187,7 @@ Series to_device_series(const HostSeries &H);
 double default_c(int quantised, double delta, double rho);
 int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolved *R);
 void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr);
+void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out);
 }  // namespace rl0
 
 // ---- helpers shared by translation units -------------------------------
@@ -193,3 +203,7 @@ int rl0_workspace_alloc(rl0_expander *A);
 void rl0_workspace_free(rl0_expander *A);
 
 static inline unsigned rl0_div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Rows of a residual-code buffer (a multiple of 8, so that its bytes are a
+// multiple of 16 and one bulk copy moves it).
+__host__ __device__ static inline long long rl0_code_rows(long long m) { return (m + 7) / 8 * 8; }

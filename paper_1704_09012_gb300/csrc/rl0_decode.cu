@@ -19,6 +19,7 @@
 //                 advances t and sets the done flag (converged or t <= 0).
 // No float atomics anywhere: every sum has a fixed order, so results do not
 // depend on the launch configuration or on scheduling.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,6 +28,7 @@
 
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
+#include "rl0_round.cuh"
 #include <cuda_bf16.h>
 
 #define CK(call)                                          \
@@ -35,24 +37,6 @@
         if (e_ != cudaSuccess) return rl0_cuda_err(e_);   \
     } while (0)
 
-// Fixed pointers and sizes of one expander's decode, passed by value.
-struct KArgs {
-    int n, m, d, nchunks, nsm;
-    const int32_t *rows_sm, *rows_cm, *rowptr, *colidx;
-    float2 *rz0, *rz1;
-    int *list;
-    UndoEntry *ulog, *dlog;
-    int *bcnt, *bkt;
-    double *l1part;
-    unsigned long long *hkkey;
-    DecodeState *st;
-    DecodeCtx *ctx;
-    const RoundThr *thr;
-    RoundLog *rlog;
-    double *final_part;
-    cudaGraphConditionalHandle cond;   // while-loop condition of the round graph
-    int has_cond;
-};
 
 // r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
 // chunk (one row per thread, blockDim = RL0_ROWS_CHUNK).
@@ -69,6 +53,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
         if (!isfinite(r)) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
         const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
         rz[i] = make_float2(r, z);
+        if (a.res_ok) (dst ? a.code1 : a.code0)[i] = residual_code(r);
         l1 = fabs((double)r);
     }
     const double s = block_sum_f64(l1, sh);
@@ -299,63 +284,13 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
         }
         if (tid == 0) S.nq = 0;
     }
-    const bool pass = best >= 0;
-    float old = 0.0f, nv = 0.0f;
-    if (pass) {
-        float *x = ctx->x;
-        old = x[j];
-        nv = old + bw;
-        x[j] = nv;
-    }
-    if (ctx->passed && active) ctx->passed[j] = pass ? 1 : 0;
-    const int lane = threadIdx.x & 31;
-    unsigned mask = __ballot_sync(0xffffffffu, pass);
-    if (mask) {
-        const int leader = __ffs(mask) - 1;
-        const int dn = __reduce_add_sync(0xffffffffu, pass ? (int)(nv != 0.0f) - (int)(old != 0.0f) : 0);
-        const unsigned gone = __popc(__ballot_sync(0xffffffffu, pass && old != 0.0f && nv == 0.0f));
-        unsigned base = 0;
-        if (lane == leader) {
-            if (dn) atomicAdd(&a.st->nnz_delta, dn);
-            if (gone) atomicAdd(&a.st->zeroed, gone);
-            base = atomicAdd(&a.st->upd_count, (unsigned)__popc(mask));
-        }
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (pass) {
-            UndoEntry e;
-            e.j = j;
-            e.old = old;
-            a.ulog[base + __popc(mask & ((1u << lane) - 1u))] = e;
-        }
-        const bool fresh = pass && old == 0.0f && nv != 0.0f;
-        mask = __ballot_sync(0xffffffffu, fresh);
-        if (mask) {
-            const int ld2 = __ffs(mask) - 1;
-            if (lane == ld2) base = atomicAdd(&a.st->list_count, (unsigned)__popc(mask));
-            base = __shfl_sync(0xffffffffu, base, ld2);
-            if (fresh) a.list[base + __popc(mask & ((1u << lane) - 1u))] = j;
-        }
-    }
+    commit_column(a, ctx, j, active, best, bw);
 }
 
-// The launch's last CTA applies H_k when |supp x'| > k (state read past L1,
-// since other CTAs updated it during this launch).
 template <int DMAX, int NT, bool LEARNED>
 __device__ __forceinline__ void col_last_cta(const KArgs &a, const DecodeCtx *ctx, ColShared<DMAX, NT, LEARNED> &S)
 {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) S.last = (atomicAdd(&a.st->col_done, 1u) == gridDim.x - 1u);
-    __syncthreads();
-    if (!S.last) return;
-    __threadfence();
-    DecodeState *stw = a.st;
-    const unsigned upd = __ldcg(&stw->upd_count);
-    const long long nnz = (long long)__ldcg(&stw->nnz) + __ldcg(&stw->nnz_delta);
-    if (threadIdx.x == 0) stw->col_done = 0u;
-    if (upd == 0 || nnz <= ctx->k) return;
-    cta_hk_select<NT>(a.list, __ldcg(&stw->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &stw->drop_count, S.h.hk,
-                      S.h.suf);
+    last_cta_hk<NT>(a, ctx, S.h.hk, S.h.suf, &S.last);
 }
 
 template <int DMAX, bool IND, bool LEARNED>
@@ -489,7 +424,8 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
         st->iters += 1;
         st->l1_new = l1n;
         st->converged = (st->l1_hat <= ctx->stop_level);
-        if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds) st->done = 1;
+        if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds || st->status != 0)
+            st->done = 1;
         if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
     }
 }
@@ -535,6 +471,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
         const float r = ctx->y[i] - sum;
         const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
         rz[i] = make_float2(r, z);
+        if (a.res_ok) (st->cur ? a.code0 : a.code1)[i] = residual_code(r);
         l1 = fabs((double)r);
     }
     const double s = block_sum_f64(l1, sh);
@@ -591,6 +528,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
         const float r = ctx->y[i] - sum;
         if (!isfinite(ctx->y[i])) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
         a.rz0[i] = make_float2(r, ctx->indicator ? 0.0f : series_eval(ctx->pz, r));
+        if (a.res_ok) a.code0[i] = residual_code(r);
         l1 = fabs((double)r);
     }
     const double s = block_sum_f64(l1, sh);
@@ -699,6 +637,9 @@ KArgs make_args(const rl0_expander *A)
     a.colidx = A->colidx;
     a.rz0 = w.rz[0];
     a.rz1 = w.rz[1];
+    a.code0 = w.code[0];
+    a.code1 = w.code[1];
+    a.pzlb = w.pzlb;
     a.list = w.list;
     a.ulog = w.ulog;
     a.dlog = w.dlog;
@@ -711,11 +652,14 @@ KArgs make_args(const rl0_expander *A)
     a.thr = w.thr;
     a.rlog = w.rlog;
     a.final_part = w.final_part;
+    a.res_list = w.res_list;
+    rl0_res_setup(A, &a);
     return a;
 }
 
 void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
+    if (!learned && rl0_res_launch(a, indicator, s)) return;
 #define RL0_CS(D, I, L) k_column_score<D, I, L><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
     if (learned) {
         if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }
@@ -845,6 +789,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
 // Pinned host staging: ctx, thresholds, state, final partials, log.
 struct HostStage {
     DecodeCtx ctx;
+    float pzlb[RL0_PZ_BINS];
     DecodeState st;
     RoundThr thr[RL0_MAX_ROUNDS];
     RoundLog log[RL0_MAX_ROUNDS];
@@ -858,6 +803,8 @@ struct TableCache {
     int nrounds = 0;
     DecodeCtx ctx;
     RoundThr thr[RL0_MAX_ROUNDS];
+    bool pz_valid = false;
+    float pzlb[RL0_PZ_BINS];
 };
 
 }  // namespace
@@ -875,6 +822,10 @@ int rl0_workspace_alloc(rl0_expander *A)
     auto al = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
     al((void **)&w.rz[0], m * sizeof(float2));
     al((void **)&w.rz[1], m * sizeof(float2));
+    al((void **)&w.code[0], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
+    al((void **)&w.code[1], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
+    al((void **)&w.pzlb, RL0_PZ_BINS * sizeof(float));
+    al((void **)&w.res_list, n * sizeof(int));
     al((void **)&w.list, n * sizeof(int));
     al((void **)&w.list_tmp, sizeof(int));
     al((void **)&w.ulog, n * sizeof(UndoEntry));
@@ -934,7 +885,7 @@ void rl0_workspace_free(rl0_expander *A)
         delete (TableCache *)A->table_cache;
         A->table_cache = nullptr;
     }
-    void *ptrs[] = {w.rz[0], w.rz[1], w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt, w.l1part,
+    void *ptrs[] = {w.rz[0], w.rz[1], w.code[0], w.code[1], w.pzlb, w.res_list, w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt, w.l1part,
                     w.hk_scratch, w.st, w.ctx, w.thr, w.rlog, w.final_part};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&w, 0, sizeof(w));
@@ -960,12 +911,28 @@ static void cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeC
     }
     rl0::fill_tables(A->m, A->d, k, R, ctx, thr, R.nrounds);
     if (tc) {
+        tc->pz_valid = false;
         tc->valid = true;
         tc->k = k;
         tc->p = R.p;
         tc->nrounds = R.nrounds;
         tc->ctx = *ctx;
         std::memcpy(tc->thr, thr, R.nrounds * sizeof(RoundThr));
+    }
+}
+
+// p_z lower bounds of the parameter set cached_tables just resolved.
+static void cached_pz(rl0_expander *A, int64_t k, const Resolved &R, float *out)
+{
+    TableCache *tc = (TableCache *)A->table_cache;
+    if (tc && tc->valid && tc->pz_valid) {
+        std::memcpy(out, tc->pzlb, sizeof(tc->pzlb));
+        return;
+    }
+    rl0::pz_lower_bounds(A->m, A->d, k, R, out);
+    if (tc && tc->valid) {
+        std::memcpy(tc->pzlb, out, sizeof(tc->pzlb));
+        tc->pz_valid = true;
     }
 }
 
@@ -985,6 +952,10 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    if (!R.indicator && R.p.scorer == 0) {
+        cached_pz(A, k, R, H->pzlb);
+        CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     const int dmax = dmax_of(A->d);
     GraphCache *gc = (GraphCache *)A->graph_cache;
@@ -1043,7 +1014,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         }
     }
     A->last_log_rounds = H->st.rounds_run;
-    if (H->st.status) return RL0_ERR_TIMEOUT;
+    if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
     if (learned && !(H->st.l1_hat <= R.keep_level)) {
         // The learned decode's residual is not consistent with the noise
         // (||r||_1 > E||eta||_1 + 3 sqrt(Var||eta||_1)): Algorithm 2 with the
@@ -1074,7 +1045,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         if (stats) CK(cudaEventRecord(ev[1], s));
         CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (H->st.status) return RL0_ERR_TIMEOUT;
+        if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
         if (stats) {
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, ev[0], ev[1]);
@@ -1174,6 +1145,10 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    if (!R.indicator && R.p.scorer == 0) {
+        rl0::pz_lower_bounds(A->m, A->d, k, R, H->pzlb);
+        CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     const KArgs a = make_args(A);
     k_copy_f<<<2 * a.nsm, 256, 0, s>>>(xhat_dev, xp_dev, a.n);
@@ -1304,6 +1279,10 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     a.ctx = (DecodeCtx *)(base + L.ctx);
     a.thr = (const RoundThr *)(base + L.thr);
     a.rlog = (RoundLog *)(base + L.rlog);
+    a.code0 = a.code1 = nullptr;                  // no residual codes: the L2 column kernel
+    a.pzlb = nullptr;
+    a.res_list = nullptr;
+    a.res_ok = 0;
 
     // Per-call tables go through the expander's pinned staging block, which was
     // set up when the expander was created.

@@ -3,6 +3,8 @@
 // order (Robust-l0, arXiv 1704.09012, Algorithm 2).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "rl0_common.cuh"
 
 // ---------------------------------------------------------------------------
@@ -106,6 +108,36 @@ __device__ __forceinline__ AnchorEval eval_anchor(const float *rc, int stride, i
     return E;
 }
 
+// eval_anchor on a column held in registers (r[l], l < d): the same FP32
+// operations in the same order, so the results are bitwise those of eval_anchor.
+template <int DMAX, bool IND>
+__device__ __forceinline__ AnchorEval eval_anchor_regs(const float *r, int d, int s, float te, const Series &pe)
+{
+    float rs = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DMAX; ++l)
+        if (l == s) rs = r[l];
+    float ne = 0.0f, num = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DMAX; ++l) {
+        if (l < d) {
+            const float rl = r[l];
+            const float q = IND ? (fabsf(rs - rl) <= te ? 1.0f : 0.0f) : series_eval(pe, rs - rl);
+            ne += q;
+            num += rl * q;
+        }
+    }
+    AnchorEval E;
+    E.ne = ne;
+    E.w = num / ne;
+    float lhs = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DMAX; ++l)
+        if (l < d) lhs += fabsf(r[l] - E.w);
+    E.lhs = lhs;
+    return E;
+}
+
 // Alg. 2's pass test: l1 decrease over the column and n_e - n_z >= alpha.
 template <bool IND>
 __device__ __forceinline__ bool score_anchor(const float *rc, int stride, int d, int s, float te,
@@ -192,12 +224,14 @@ __device__ __forceinline__ float mlp_logit(const float *W, const float *f)
 
 // Fast-path bound of Alg. 2's test for every anchor of a column held in
 // registers: the anchors (|r_i| >= ta) whose n_e can still reach n_z + need.
-//  - 0/1 scores: n_e = 1 + #{l != i : |r_i - r_l| <= te} exactly;
-//  - continuous scores: q_e(D) = 0 beyond the cut (reach) and otherwise
-//    q_e(D) <= 1 / (1 + c1 (u + u^2/2)), u = b1 D^2 (b1 the smallest b_q of the
-//    q >= 1 terms, c1 = 1 - a_0), so n_e <= 1 + the sum of these bounds.
-// Callers pass need = alpha for the 0/1 scores and alpha - 1e-3 for the
-// continuous ones (the slack covers FP32 rounding in the bound and in n_e).
+// First level, both score kinds: n_e <= 1 + #{l != i : |r_i - r_l| <= reach}
+// (exact for the 0/1 scores, where reach = te).  Second level, continuous
+// scores, only for the anchors that survive the first: q_e(D) <=
+// 1 / (1 + c1 (u + u^2/2)), u = b1 D^2 (b1 the smallest b_q of the q >= 1
+// terms, c1 = 1 - a_0, from e^x >= 1 + x + x^2/2), so n_e <= 1 + the sum of
+// these bounds over the near partners.  Callers pass need = alpha for the 0/1
+// scores and alpha - 1e-3 for the continuous ones (the slack covers FP32
+// rounding in the bound, the approximate reciprocal and n_e itself).
 template <int DMAX, bool IND>
 __device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, float ta, float reach, float b1,
                                                       float c1, float nz, float need)
@@ -207,32 +241,164 @@ __device__ __forceinline__ unsigned anchor_candidates(const float *r, int d, flo
     for (int s = 0; s < DMAX; ++s)
         if (s < d && fabsf(r[s]) >= ta) amask |= 1u << s;
     if (!amask) return 0u;
-    float ub[DMAX];
+    unsigned nm[DMAX];
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) ub[s] = 1.0f;
+    for (int s = 0; s < DMAX; ++s) nm[s] = 0u;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
 #pragma unroll
         for (int l = s + 1; l < DMAX; ++l) {
-            if (l < d) {
-                const float D = r[s] - r[l];
-                if (fabsf(D) <= reach) {
-                    float q = 1.0f;
-                    if (!IND) {
-                        const float u = b1 * (D * D);
-                        q = __frcp_rn(fmaf(c1, fmaf(0.5f * u, u, u), 1.0f));
-                    }
-                    ub[s] += q;
-                    ub[l] += q;
-                }
+            if (l < d && fabsf(r[s] - r[l]) <= reach) {
+                nm[s] |= 1u << l;
+                nm[l] |= 1u << s;
             }
         }
     }
     unsigned cand = 0;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)
-        if (((amask >> s) & 1u) && ub[s] - nz >= need) cand |= 1u << s;
-    return cand;
+        if (((amask >> s) & 1u) && (1.0f + (float)__popc(nm[s])) - nz >= need) cand |= 1u << s;
+    if (IND || !cand) return cand;
+    unsigned out = 0;
+    for (unsigned rest = cand; rest; rest &= rest - 1) {
+        const int s = __ffs(rest) - 1;
+        float rs = 0.0f;
+        unsigned ns = 0u;
+#pragma unroll
+        for (int l = 0; l < DMAX; ++l)
+            if (l == s) {
+                rs = r[l];
+                ns = nm[l];
+            }
+        float ub = 1.0f;
+#pragma unroll
+        for (int l = 0; l < DMAX; ++l) {
+            if ((ns >> l) & 1u) {
+                const float u = b1 * ((rs - r[l]) * (rs - r[l]));
+                ub += __fdividef(1.0f, fmaf(c1, fmaf(0.5f * u, u, u), 1.0f));
+            }
+        }
+        if (ub - nz >= need) out |= 1u << s;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit residual codes.  code(r) = FP16(r) rounded toward zero, its magnitude
+// clamped to 0x7bff.  For v = the code's FP16 value, |r| lies in
+// [|v|, |v| + ulp(v)) with ulp(v) <= |v| 2^-10 + 2^-24, and r has v's sign
+// (or |r| < 2^-24), so |r - v| < e(v) = |v| 2^-10 + 2^-24.  Magnitude 0x7bff
+// (65504) also stands for every larger |r|: a column holding one gets no
+// bound.  The column kernel keeps every row's code in shared memory and bounds
+// Alg. 2's test from them; only the columns that survive read the FP32
+// residuals.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned short residual_code(float r)
+{
+    unsigned b = __half_as_ushort(__float2half_rz(r));
+    if ((b & 0x7fffu) > 0x7bffu) b = (b & 0x8000u) | 0x7bffu;
+    return (unsigned short)b;
+}
+
+#define RL0_CODE_WIDEN 1.00000095367431640625f    // 1 + 2^-20
+#define RL0_CODE_NARROW 0.99999904632568359375f   // 1 - 2^-20
+#define RL0_CODE_EREL 9.7656343132257461548e-4f   // 2^-10 (1 + 2^-20), rounded up
+#define RL0_CODE_EABS 5.9604701102204882773e-8f   // 2^-24 (1 + 2^-20), rounded up
+
+// Per-launch thresholds of the code bound, from the round's FP32 thresholds:
+// an anchor (|r| >= ta) needs |v| >= ta_lo, a row with |v| <= tz_in has
+// |r| <= tz, and reach1 = reach widened by 2^-20 (covers the FP32 rounding of
+// the near test here and in the exact path).
+struct CodeThr {
+    float ta_lo, tz_in, reach1;
+};
+
+__device__ __forceinline__ CodeThr code_thresholds(float ta, float tz, float reach)
+{
+    // |r| < |v| (1 + 2^-10) + 2^-24 and 1 / (1 + 2^-10) >= 1 - 2^-10
+    CodeThr c;
+    c.ta_lo = (ta - 5.9604644775390625e-8f) * 0.9990224838256836f * RL0_CODE_NARROW;
+    c.tz_in = (tz - 5.9604644775390625e-8f) * 0.9990224838256836f * RL0_CODE_NARROW;
+    c.reach1 = reach * RL0_CODE_WIDEN;
+    return c;
+}
+
+// The bound of anchor_candidates taken over every residual the codes allow:
+//  - anchor possible when |v| >= ta_lo;
+//  - near possible when |v_s - v_l| <= reach1 + e_s + e_l;
+//  - n_z at least the sum of pzlb over the rows' bins (0/1 scores: the count
+//    of rows with |v| <= tz_in);
+//  - continuous scores: for the anchors left, q_e at most
+//    1 / (1 + c1 (u + u^2/2)) at the smallest |D| the codes allow.
+// Returns a superset of anchor_candidates on the FP32 residuals.
+template <int DMAX, bool IND>
+__device__ __forceinline__ unsigned code_candidates(const unsigned short *codes, const float *pzlb, const int *rid,
+                                                    int d, const CodeThr &ct, float b1, float c1, float need)
+{
+    float v[DMAX], e[DMAX];
+    unsigned amask = 0, bmax = 0;
+    float nzlb = 0.0f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        v[s] = 0.0f;
+        e[s] = 0.0f;
+        if (s < d) {
+            const unsigned c = codes[rid[s]];
+            const float vv = __half2float(__ushort_as_half((unsigned short)c));
+            const float av = fabsf(vv);
+            v[s] = vv;
+            e[s] = fmaf(av, RL0_CODE_EREL, RL0_CODE_EABS);
+            bmax = max(bmax, c & 0x7fffu);
+            if (av >= ct.ta_lo) amask |= 1u << s;
+            nzlb += IND ? (av <= ct.tz_in ? 1.0f : 0.0f) : pzlb[(c & 0x7fffu) >> RL0_PZ_SHIFT];
+        }
+    }
+    if (!amask) return 0u;
+    if (bmax >= 0x7bffu) return amask;            // a saturated code: no bound
+    int cnt[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) cnt[s] = 0;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        const float rs = ct.reach1 + e[s];
+#pragma unroll
+        for (int l = s + 1; l < DMAX; ++l) {
+            if (l < d && fabsf(v[s] - v[l]) <= rs + e[l]) {
+                ++cnt[s];
+                ++cnt[l];
+            }
+        }
+    }
+    // candidate: 1 + near count - n_z >= need, i.e. near count >= ceil(need - 1 + n_z)
+    const int kneed = (int)ceilf(need - 1.0f + nzlb);
+    unsigned cand = 0;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s)
+        if (((amask >> s) & 1u) && cnt[s] >= kneed) cand |= 1u << s;
+    if (IND || !cand) return cand;
+    unsigned out = 0;
+    for (unsigned rest = cand; rest; rest &= rest - 1) {
+        const int s = __ffs(rest) - 1;
+        float vs = 0.0f, es = 0.0f;
+#pragma unroll
+        for (int l = 0; l < DMAX; ++l)
+            if (l == s) {
+                vs = v[l];
+                es = e[l];
+            }
+        const float rs = ct.reach1 + es;
+        float ub = 1.0f;
+#pragma unroll
+        for (int l = 0; l < DMAX; ++l) {
+            if (l < d && l != s && fabsf(vs - v[l]) <= rs + e[l]) {
+                const float D = fmaxf(fabsf(vs - v[l]) - (es + e[l]), 0.0f) * RL0_CODE_NARROW;
+                const float u = b1 * (D * D);
+                ub += __fdividef(1.0f, fmaf(c1, fmaf(0.5f * u, u, u), 1.0f));
+            }
+        }
+        if (ub - nzlb >= need) out |= 1u << s;
+    }
+    return out;
 }
 
 // ---------------------------------------------------------------------------
@@ -267,10 +433,9 @@ __device__ void cta_hk_select(const int *list, unsigned total, float *x, long lo
     }
     if (t == 0) { sm.prefix = 0ull; sm.need = (unsigned)k; }
     __syncthreads();
-    const int shifts[6] = {52, 41, 30, 19, 8, 0};
-    const int widths[6] = {11, 11, 11, 11, 11, 8};
     for (int p = 0; p < 6; ++p) {
-        const int sh = shifts[p], wd = widths[p];
+        // digits of 11 bits from bit 63 down (shifts 52, 41, 30, 19, 8), then the last 8
+        const int sh = (p < 5) ? 52 - 11 * p : 0, wd = (p < 5) ? 11 : 8;
         const int nb = 1 << wd;
         for (int b = t; b < HK_BINS; b += NT) sm.hist[b] = 0;
         const unsigned long long prefix = sm.prefix;

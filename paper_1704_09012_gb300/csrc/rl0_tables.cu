@@ -304,4 +304,35 @@ void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx,
     }
 }
 
+// Value of a non-negative FP16 bit pattern (0 .. 0x7c00; 0x7c00 is +inf).
+static double half_bits_value(unsigned h)
+{
+    const unsigned e = h >> 10, f = h & 0x3ffu;
+    if (e == 31) return INFINITY;
+    if (e == 0) return std::ldexp((double)f, -24);
+    return std::ldexp((double)(1024u + f), (int)e - 25);
+}
+
+// Lower bounds of p_z over the 16-bit residual codes.  A code of magnitude
+// bits b stands for |r| < the FP16 value of b + 1, and p_breve_z is
+// decreasing in |r| (1/p_breve_z = sum of positive a_q exp(b_q w^2)), so over
+// bin c = b >> RL0_PZ_SHIFT the posterior is at least p_breve_z at the
+// FP16 value of (c + 1) << RL0_PZ_SHIFT.  The factor 1 - 1e-5 covers the FP32
+// evaluation on the device; past the series cut the device takes 0.
+void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out)
+{
+    const rl0_params &p = R.p;
+    if (!(p.sigma_n > 0.0)) {
+        for (int c = 0; c < RL0_PZ_BINS; ++c) out[c] = 0.0f;
+        return;
+    }
+    const double rho = (double)k / (double)m;
+    const HostSeries hz = make_series(d * rho, p.sigma_s * p.sigma_s, p.sigma_n * p.sigma_n, p.ell);
+    const double cut = (double)to_device_series(hz).cut;
+    for (int c = 0; c < RL0_PZ_BINS; ++c) {
+        const double U = half_bits_value((unsigned)(c + 1) << RL0_PZ_SHIFT);
+        out[c] = (U > cut) ? 0.0f : (float)((1.0 - 1e-5) / series_F(hz, U));
+    }
+}
+
 }  // namespace rl0
