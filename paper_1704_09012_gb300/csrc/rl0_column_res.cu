@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         const int j = j0 + tid;
         const bool active = j < hi;
         const bool cand =
-            active && code_candidates<DMAX, IND>(s_code, s_pz, rid, d, ct, b1, c1, need) != 0u;
+            active && code_candidates<DMAX, IND>(s_code, s_pz, rid, d, ct, need) != 0u;
         const unsigned m = __ballot_sync(0xffffffffu, cand);
         if (m) {
             const int leader = __ffs(m) - 1;

@@ -325,15 +325,16 @@ __device__ __forceinline__ CodeThr code_thresholds(float ta, float tz, float rea
 
 // The bound of anchor_candidates taken over every residual the codes allow:
 //  - anchor possible when |v| >= ta_lo;
-//  - near possible when |v_s - v_l| <= reach1 + e_s + e_l;
+//  - near possible when |v_s - v_l| <= reach1 + 2 max_l e_l;
 //  - n_z at least the sum of pzlb over the rows' bins (0/1 scores: the count
 //    of rows with |v| <= tz_in);
-//  - continuous scores: for the anchors left, q_e at most
-//    1 / (1 + c1 (u + u^2/2)) at the smallest |D| the codes allow.
-// Returns a superset of anchor_candidates on the FP32 residuals.
+//  - n_e at most 1 + the number of rows that can be near (q_e <= 1).
+// Returns a superset of the anchors that pass Alg. 2's test on the FP32
+// residuals (the resolve then applies anchor_candidates' tighter bound to the
+// few survivors: here, per column, it would cost more than it saves).
 template <int DMAX, bool IND>
 __device__ __forceinline__ unsigned code_candidates(const unsigned short *codes, const float *pzlb, const int *rid,
-                                                    int d, const CodeThr &ct, float b1, float c1, float need)
+                                                    int d, const CodeThr &ct, float need)
 {
     float v[DMAX], e[DMAX];
     unsigned amask = 0, bmax = 0;
@@ -355,50 +356,35 @@ __device__ __forceinline__ unsigned code_candidates(const unsigned short *codes,
     }
     if (!amask) return 0u;
     if (bmax >= 0x7bffu) return amask;            // a saturated code: no bound
-    int cnt[DMAX];
+    // near possible: |v_s - v_l| <= reach1 + 2 max_l e_l (>= reach1 + e_s + e_l).
+    // Counted on the FMA pipe: q = sat((thr - |v_s - v_l|) 2^100 + 2^10) is 1
+    // when the pair can be near, 0 when thr - |v_s - v_l| < -2^-90, and in
+    // between only within 2^-90 of the test (an over-count, still a bound).
+    float emax = 0.0f;
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) cnt[s] = 0;
+    for (int s = 0; s < DMAX; ++s) emax = fmaxf(emax, e[s]);
+    const float thr = fmaf(2.0f, emax, ct.reach1);
+    float cnt[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) cnt[s] = 0.0f;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
-        const float rs = ct.reach1 + e[s];
 #pragma unroll
         for (int l = s + 1; l < DMAX; ++l) {
-            if (l < d && fabsf(v[s] - v[l]) <= rs + e[l]) {
-                ++cnt[s];
-                ++cnt[l];
+            if (l < d) {
+                const float q = __saturatef(fmaf(thr - fabsf(v[s] - v[l]), 0x1p100f, 0x1p10f));
+                cnt[s] += q;
+                cnt[l] += q;
             }
         }
     }
-    // candidate: 1 + near count - n_z >= need, i.e. near count >= ceil(need - 1 + n_z)
-    const int kneed = (int)ceilf(need - 1.0f + nzlb);
+    // candidate: 1 + near count - n_z >= need
+    const float kneed = need - 1.0f + nzlb;
     unsigned cand = 0;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)
         if (((amask >> s) & 1u) && cnt[s] >= kneed) cand |= 1u << s;
-    if (IND || !cand) return cand;
-    unsigned out = 0;
-    for (unsigned rest = cand; rest; rest &= rest - 1) {
-        const int s = __ffs(rest) - 1;
-        float vs = 0.0f, es = 0.0f;
-#pragma unroll
-        for (int l = 0; l < DMAX; ++l)
-            if (l == s) {
-                vs = v[l];
-                es = e[l];
-            }
-        const float rs = ct.reach1 + es;
-        float ub = 1.0f;
-#pragma unroll
-        for (int l = 0; l < DMAX; ++l) {
-            if (l < d && l != s && fabsf(vs - v[l]) <= rs + e[l]) {
-                const float D = fmaxf(fabsf(vs - v[l]) - (es + e[l]), 0.0f) * RL0_CODE_NARROW;
-                const float u = b1 * (D * D);
-                ub += __fdividef(1.0f, fmaf(c1, fmaf(0.5f * u, u, u), 1.0f));
-            }
-        }
-        if (ub - nzlb >= need) out |= 1u << s;
-    }
-    return out;
+    return cand;
 }
 
 // ---------------------------------------------------------------------------
