@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
     const float need = IND ? ctx->alpha : ctx->alpha - 1e-3f;
     int32_t *passed = ctx->passed;
     const int lane = tid & 31;
-    int *seg = a.res_list + lo;                    // this CTA's slice of the survivor list
+    // this CTA's slice of the survivor list: entries (j, its d row ids)
+    int *seg = a.res_list + (size_t)lo * (size_t)(DMAX + 1);
     for (; j0 < hi; j0 += NT) {
         int rid[DMAX];
 #pragma unroll
@@ -199,7 +200,13 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
             if (lane == leader) base = atomicAdd(&S.count, __popc(m));
             base = __shfl_sync(0xffffffffu, base, leader);
             const int pos = base + __popc(m & ((1u << lane) - 1u));
-            if (cand && pos < hi - lo) seg[pos] = j;   // pos < hi - lo always: one entry per column
+            if (cand && pos < hi - lo) {            // pos < hi - lo always: one entry per column
+                int *ent = seg + (size_t)pos * (DMAX + 1);
+                ent[0] = j;
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s)
+                    if (s < d) ent[1 + s] = rid[s];
+            }
         }
         if (passed && active && !cand) passed[j] = 0;
     }
@@ -212,12 +219,15 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         // one thread per listed column: FP32 residuals, exact candidates
         const int e = b0 + tid;
         const bool act = e < count;
-        const int j = act ? __ldcg(seg + e) : 0;
+        const int *ent = seg + (size_t)(act ? e : 0) * (DMAX + 1);
+        const int j = act ? __ldcg(ent) : 0;
         unsigned cand = 0u;
+        float old = 0.0f;
         if (act) {
             int rid[DMAX];
 #pragma unroll
-            for (int s = 0; s < DMAX; ++s) rid[s] = (s < d) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+            for (int s = 0; s < DMAX; ++s) rid[s] = (s < d) ? __ldcg(ent + 1 + s) : 0;
+            old = ctx->x[j];
             float r[DMAX];
             float nz = 0.0f, rhs = 0.0f;
 #pragma unroll
@@ -252,7 +262,10 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         __syncthreads();
         for (unsigned k = tid; k < nitems; k += NT) {
             const int ee = R.it_e[k], sl = R.it_s[k];
-            const AnchorEval E = eval_anchor<IND>(&R.r[0][ee], NT, d, sl, th.te, S.pe);
+            float re[DMAX];
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) re[s] = R.r[s][ee];
+            const AnchorEval E = eval_anchor_regs<DMAX, IND>(re, d, sl, th.te, S.pe);
             R.it_ok[k] = (E.lhs <= R.rhs[ee] && E.ne - R.nz[ee] >= alpha) ? 1 : 0;
             R.it_w[k] = E.w;
         }
@@ -267,9 +280,8 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
                 break;
             }
         const bool pass = best >= 0;
-        float old = 0.0f, nv = 0.0f;
+        float nv = old;
         if (pass) {
-            old = ctx->x[j];
             nv = old + bw;
             ctx->x[j] = nv;
         }
@@ -347,6 +359,8 @@ int res_nt(int d)
 }
 
 }  // namespace
+
+int rl0_res_dmax(int d) { return res_variant(d); }
 
 void rl0_res_setup(const rl0_expander *A, KArgs *a)
 {

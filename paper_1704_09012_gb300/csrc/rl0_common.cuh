@@ -125,7 +125,7 @@ struct Workspace {
     float2 *rz[2];            // (r_i, p_z(r_i)) for r_hat and the candidate r
     unsigned short *code[2];  // 16-bit codes of the same residuals, padded to a multiple of 8 rows
     float *pzlb;              // p_z lower bound per code bin, float[RL0_PZ_BINS]
-    int *res_list;            // survivors of the column kernel's code bound, int[n]
+    int *res_list;            // survivors of the column kernel's code bound, n entries (rl0_res_dmax)
     int *list;                // support + new nonzeros, capacity n
     int *list_tmp;            // compaction scratch, capacity n
     UndoEntry *ulog;          // updates of this round, capacity n
@@ -138,7 +138,7 @@ struct Workspace {
     DecodeCtx *ctx;
     RoundThr *thr;            // per-round thresholds, capacity RL0_MAX_ROUNDS
     RoundLog *rlog;           // per-round log, capacity RL0_MAX_ROUNDS
-    double *final_part;       // FP64 final-residual partials
+    double *final_part;       // FP64 residual-norm partials, one set per rz buffer (2 x chunks)
     int max_rounds;
 };
 

@@ -57,7 +57,11 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
         l1 = fabs((double)r);
     }
     const double s = block_sum_f64(l1, sh);
-    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+    if (threadIdx.x == 0) {
+        a.l1part[blockIdx.x] = s;
+        // r = y_hat with x_hat = 0: the FP64 residual-norm partial is the same sum
+        if (!src_override) a.final_part[(size_t)dst * a.nchunks + blockIdx.x] = s;
+    }
 }
 
 // Zero the working x.
@@ -432,7 +436,7 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
 
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
 {
-    __shared__ double sh[RL0_ROWS_CHUNK];
+    __shared__ double2 sh2[RL0_ROWS_CHUNK];
     __shared__ unsigned s_scan[RL0_ROWS_CHUNK];
     __shared__ int s_last;
     DecodeState *st = a.st;
@@ -447,12 +451,17 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     const DecodeCtx *ctx = a.ctx;
     const float *x = ctx->x;
     float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
-    double l1 = 0.0;
+    double l1 = 0.0, f1 = 0.0;
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
     if (i < a.m) {
         float sum = 0.0f;
+        double acc = (double)ctx->y[i];             // the same row in FP64, ascending columns
         if (csr) {
-            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
+            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
+                const float xv = x[a.colidx[p]];
+                sum += xv;
+                acc -= (double)xv;
+            }
             a.bcnt[i] = 0;
         } else {
             const int c = a.bcnt[i];
@@ -464,7 +473,11 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
                 sort8(js);                              // ascending column order
 #pragma unroll
                 for (int q = 0; q < RL0_BUCKET; ++q)
-                    if (q < c) sum += x[js[q]];
+                    if (q < c) {
+                        const float xv = x[js[q]];
+                        sum += xv;
+                        acc -= (double)xv;
+                    }
                 a.bcnt[i] = 0;
             }
         }
@@ -473,9 +486,14 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
         rz[i] = make_float2(r, z);
         if (a.res_ok) (st->cur ? a.code0 : a.code1)[i] = residual_code(r);
         l1 = fabs((double)r);
+        f1 = fabs(acc);
     }
-    const double s = block_sum_f64(l1, sh);
-    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+    // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 with every step FP64
+    const double2 s2 = block_sum2_f64(l1, f1, sh2);
+    if (threadIdx.x == 0) {
+        a.l1part[blockIdx.x] = s2.x;
+        a.final_part[(size_t)(st->cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
+    }
     if (no_accept) return;
     // ---- the launch's last CTA accepts or undoes the round
     __threadfence();
@@ -488,27 +506,15 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     accept_step<RL0_ROWS_CHUNK>(a, upd, s_scan);
 }
 
-// ||y - A x_hat||_1 with every step in FP64 (the final residual-norm check).
-__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_final_l1(KArgs a)
-{
-    __shared__ double sh[RL0_ROWS_CHUNK];
-    const float *x = a.ctx->x;
-    double l1 = 0.0;
-    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    if (i < a.m) {
-        double acc = (double)a.ctx->y[i];
-        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) acc -= (double)x[a.colidx[p]];
-        l1 = fabs(acc);
-    }
-    const double s = block_sum_f64(l1, sh);
-    if (threadIdx.x == 0) a.final_part[blockIdx.x] = s;
-}
-
-// Sum of the FP64 final-residual partials in chunk order (one warp).
+// ||y_hat - A x_hat||_1 with every step in FP64 (the final residual-norm
+// check): the chunk partials of r_hat, formed in FP64 by the kernel that built
+// it (rows summed in ascending column order, 256-row trees), summed in chunk
+// order by one warp.
 __global__ void k_final_sum(KArgs a)
 {
+    const double *part = a.final_part + (size_t)a.st->cur * a.nchunks;
     double v = 0.0;
-    for (int c = threadIdx.x; c < a.nchunks; c += 32) v += a.final_part[c];
+    for (int c = threadIdx.x; c < a.nchunks; c += 32) v += part[c];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (threadIdx.x == 0) a.st->final_l1 = v;
 }
@@ -522,17 +528,28 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
     const float *x = ctx->x;
     double l1 = 0.0;
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    double f1 = 0.0;
     if (i < a.m) {
         float sum = 0.0f;
-        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) sum += x[a.colidx[p]];
+        double acc = (double)ctx->y[i];
+        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
+            const float xv = x[a.colidx[p]];
+            sum += xv;
+            acc -= (double)xv;
+        }
         const float r = ctx->y[i] - sum;
         if (!isfinite(ctx->y[i])) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
         a.rz0[i] = make_float2(r, ctx->indicator ? 0.0f : series_eval(ctx->pz, r));
         if (a.res_ok) a.code0[i] = residual_code(r);
         l1 = fabs((double)r);
+        f1 = fabs(acc);
     }
     const double s = block_sum_f64(l1, sh);
-    if (threadIdx.x == 0) a.l1part[blockIdx.x] = s;
+    const double sf = block_sum_f64(f1, sh);
+    if (threadIdx.x == 0) {
+        a.l1part[blockIdx.x] = s;
+        a.final_part[blockIdx.x] = sf;
+    }
 }
 
 // Features of every learned-scorer candidate of one round (for training logs):
@@ -611,8 +628,8 @@ struct GraphEntry {
     std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
 
-// Kernels one decode graph launches: prologue (3), 3 per round, final check (2).
-int launches_per_decode(int nrounds) { return 3 + 3 * nrounds + 2; }
+// Kernels one decode graph launches: prologue (3), 3 per round, final check (1).
+int launches_per_decode(int nrounds) { return 3 + 3 * nrounds + 1; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -746,10 +763,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             launch_round(a, dmax, indicator, learned, s);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
-            if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_l1, a.nchunks, RL0_ROWS_CHUNK, &a, nullptr, 0)))
-                break;
-            cudaGraphNode_t n4;
-            if ((rc = add_kernel_node(g, &n4, &n3, 1, (void *)k_final_sum, 1, 32, &a, nullptr, 0))) break;
+            if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_sum, 1, 32, &a, nullptr, 0))) break;
         } while (0);
         if (rc) { cudaGetLastError(); cudaGraphDestroy(g); return rc; }
         cudaError_t e = cudaGraphInstantiate(&E->exec, g, 0);
@@ -776,7 +790,6 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         if (e == cudaSuccess) e = mark(4 * r + 3);
     }
     if (e == cudaSuccess) e = mark(4 * nrounds);
-    k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
     k_final_sum<<<1, 32, 0, s>>>(a);
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return rl0_cuda_err(e); }
@@ -825,7 +838,7 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.code[0], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
     al((void **)&w.code[1], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
     al((void **)&w.pzlb, RL0_PZ_BINS * sizeof(float));
-    al((void **)&w.res_list, n * sizeof(int));
+    al((void **)&w.res_list, n * (size_t)(rl0_res_dmax(A->d) + 1) * sizeof(int));
     al((void **)&w.list, n * sizeof(int));
     al((void **)&w.list_tmp, sizeof(int));
     al((void **)&w.ulog, n * sizeof(UndoEntry));
@@ -838,7 +851,7 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.ctx, sizeof(DecodeCtx));
     al((void **)&w.thr, RL0_MAX_ROUNDS * sizeof(RoundThr));
     al((void **)&w.rlog, RL0_MAX_ROUNDS * sizeof(RoundLog));
-    al((void **)&w.final_part, nchunks * sizeof(double));
+    al((void **)&w.final_part, 2 * nchunks * sizeof(double));   // one set per rz buffer
     if (e == cudaSuccess) e = cudaMemset(w.bcnt, 0, m * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(w.st, 0, sizeof(DecodeState));
     if (e == cudaSuccess) e = cudaMallocHost(&A->host_pinned, sizeof(HostStage));
@@ -1039,7 +1052,6 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         for (int r = 0; r < R2.nrounds; ++r) {
             launch_round(a, dmax, R2.indicator, 0, s);
         }
-        k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
         k_final_sum<<<1, 32, 0, s>>>(a);
         CK(cudaGetLastError());
         if (stats) CK(cudaEventRecord(ev[1], s));
@@ -1058,7 +1070,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
             stats->hk_rounds = first.hk_rounds + H->st.hk_rounds;
             stats->fallback_rounds = first.fallback_rounds + H->st.fallback_rounds;
             stats->analytic_rounds = H->st.rounds_run;
-            stats->launches += 4 + 3 * R2.nrounds + 2;
+            stats->launches += 4 + 3 * R2.nrounds + 1;
         }
     }
     return RL0_OK;
@@ -1211,7 +1223,7 @@ static constexpr StaticLayout static_layout()
     L.bcnt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M);
     L.bkt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M * RL0_BUCKET);
     L.l1part = o; o += RL0_STATIC_ALIGN(sizeof(double) * RL0_STATIC_CHUNKS);
-    L.final_part = o; o += RL0_STATIC_ALIGN(sizeof(double) * RL0_STATIC_CHUNKS);
+    L.final_part = o; o += RL0_STATIC_ALIGN(sizeof(double) * 2 * RL0_STATIC_CHUNKS);
     L.hkkey = o; o += RL0_STATIC_ALIGN(sizeof(unsigned long long) * RL0_STATIC_MAX_N);
     L.st = o; o += RL0_STATIC_ALIGN(sizeof(DecodeState));
     L.ctx = o; o += RL0_STATIC_ALIGN(sizeof(DecodeCtx));
@@ -1305,7 +1317,6 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     for (int r = 0; r < R.nrounds; ++r) {
         launch_round(a, dmax, R.indicator, R.p.scorer == 1, s);
     }
-    k_final_l1<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
     k_final_sum<<<1, 32, 0, s>>>(a);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&H->st, base + L.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));

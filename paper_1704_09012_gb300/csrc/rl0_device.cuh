@@ -13,26 +13,33 @@
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float series_eval(const Series &S, float w)
 {
-    if (w == 0.0f) return 1.0f;                 // p_breve(0) = 1 exactly
-    if (fabsf(w) > S.cut) return 0.0f;          // below 2^-40
+    // branch-free: the sum is formed for every w and the two special cases
+    // are selected at the end (same values as returning early)
     const float u = w * w;
     float acc;
     if (S.use_poly) {
         const float t = fmaf(u, S.inv_u2, -1.0f);
         const float t2 = 2.0f * t;
         float b1 = 0.0f, b2 = 0.0f;
-        for (int k = S.npoly - 1; k >= 1; --k) {   // Clenshaw recurrence
-            const float b0 = fmaf(t2, b1, S.poly[k] - b2);
-            b2 = b1;
-            b1 = b0;
+#pragma unroll
+        for (int k = RL0_MAXPOLY - 1; k >= 1; --k) {   // Clenshaw recurrence over k < npoly
+            if (k < S.npoly) {
+                const float b0 = fmaf(t2, b1, S.poly[k] - b2);
+                b2 = b1;
+                b1 = b0;
+            }
         }
         const float G = fmaf(t, b1, S.poly[0] - b2);
         acc = fmaf(expf(S.b1 * u), G, S.a[0]);
     } else {
         acc = S.a[0];
-        for (int q = 1; q < S.nq; ++q) acc += S.a[q] * expf(S.b[q] * u);
+#pragma unroll
+        for (int q = 1; q < RL0_MAXQ; ++q)
+            if (q < S.nq) acc += S.a[q] * expf(S.b[q] * u);
     }
-    return 1.0f / acc;
+    const float p = __frcp_rn(acc);             // = 1 / acc, correctly rounded
+    return (w == 0.0f) ? 1.0f                   // p_breve(0) = 1 exactly
+                       : (fabsf(w) > S.cut ? 0.0f : p);   // below 2^-40 beyond the cut
 }
 
 // Fixed-shape FP64 tree over `n` consecutive threads starting at `base`
@@ -54,6 +61,25 @@ __device__ __forceinline__ double group_sum_f64(double v, double *sh, int lane, 
 __device__ __forceinline__ double block_sum_f64(double v, double *sh)
 {
     return group_sum_f64(v, sh, threadIdx.x, blockDim.x);
+}
+
+// Two block_sum_f64 trees in one pass (the same adds in the same order).
+__device__ __forceinline__ double2 block_sum2_f64(double a, double b, double2 *sh)
+{
+    const int t = threadIdx.x, n = blockDim.x;
+    sh[t] = make_double2(a, b);
+    __syncthreads();
+    for (int off = n >> 1; off > 0; off >>= 1) {
+        if (t < off) {
+            const double2 u = sh[t + off];
+            sh[t].x += u.x;
+            sh[t].y += u.y;
+        }
+        __syncthreads();
+    }
+    const double2 r = sh[0];
+    __syncthreads();
+    return r;
 }
 
 // Chunk partials combined in a fixed order by one warp: lane l sums chunks

@@ -17,7 +17,7 @@ struct KArgs {
     int res_ok;                        // the column kernel holds every row's code in shared memory
     int res_grid;                      // its CTAs (one per SM)
     unsigned res_pz_off, res_s_off, res_smem;   // its dynamic shared-memory layout
-    int *res_list;                     // its survivors, int[n]: CTA b uses its own column range
+    int *res_list;                     // its survivors: n entries of (j, DMAX row ids); CTA b uses its column range
     int *list;
     UndoEntry *ulog, *dlog;
     int *bcnt, *bkt;
@@ -103,4 +103,5 @@ __device__ __forceinline__ void last_cta_hk(const KArgs &a, const DecodeCtx *ctx
 // workspace has no code buffers); rl0_res_launch launches it and returns false
 // when a.res_ok is 0.
 void rl0_res_setup(const rl0_expander *A, KArgs *a);
+int rl0_res_dmax(int d);                     // slots per survivor-list entry for degree d
 bool rl0_res_launch(const KArgs &a, int indicator, cudaStream_t s);
