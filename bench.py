@@ -115,11 +115,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The sources that define the column kernel (its translation unit and the
+# headers it includes): the recorded DRAM traffic is reported only while these
+# are unchanged since the capture.
+COLUMN_KERNEL_SOURCES = ["rl0_column_res.cu", "rl0_round.cuh", "rl0_device.cuh", "rl0_common.cuh"]
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc"))):
+    for f in COLUMN_KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "rl0.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -438,9 +445,9 @@ def main():
                      "rel_l1_err": rel_l1, "accepted_rounds": stats[-1]["accepted_rounds"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": stats[-1]["launches"] * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_column_score", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_column_score_res", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic_for("k_column_score"), "alg_bytes_per_launch": alg_bytes,
+                     "traffic": traffic_for("k_column_score_res"), "alg_bytes_per_launch": alg_bytes,
                      "avg_launch_ms": ms_score},
         "kernel_group_ms_per_decode": group_ms,
         "clocks": clk.summary(),

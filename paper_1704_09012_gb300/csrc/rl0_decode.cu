@@ -3,20 +3,22 @@
 // coefficients (host, FP64), the round kernels, and the captured CUDA graph
 // that replays the loop.
 //
-// One round, as kernels on one stream:
-//   column_score  every column j reads its d residuals (slot-major row ids,
-//                 one coalesced 4-byte load per slot per thread, L2 gathers of
-//                 (r, p_z(r))), scores every anchor (Table "scores",
-//                 Eqs. (ne_nz_1), (ne_nz_2)), applies the last passing update
-//                 to x in place and logs it for undo;
-//   hk_select     H_k on the list of nonzeros (single CTA radix select on the
-//                 63-bit key (|x_j| bits, ~j): ties go to the smaller j);
+// One round, as three kernels on one stream:
+//   column score  every column j bounds, then scores, its anchors (Table
+//                 "scores", Eqs. (ne_nz_1), (ne_nz_2)), applies the last
+//                 passing update to x in place and logs it for undo
+//                 (k_column_score_res in rl0_column_res.cu: residual codes in
+//                 shared memory; k_column_score below: L2 gathers).  The
+//                 launch's last CTA applies H_k (radix select on the 63-bit
+//                 key (|x_j| bits, ~j): ties go to the smaller j);
 //   scatter       the support's (row, column) pairs into per-row buckets;
-//   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32, with
-//                 p_z(r_i) and FP64 l1 partials over fixed 1024-row chunks
-//                 (a CSR(A^T) pass replaces it when a bucket overflows);
-//   accept        ||r||_1 < ||r_hat||_1 keeps the round, otherwise undoes it;
-//                 advances t and sets the done flag (converged or t <= 0).
+//   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32 (and
+//                 the same sum in FP64 for the final residual check), with
+//                 p_z(r_i), the residual code, and l1 partials over fixed
+//                 256-row chunks (a CSR(A^T) pass replaces it when a bucket
+//                 overflows).  The launch's last CTA accepts the round if
+//                 ||r||_1 < ||r_hat||_1 or undoes it, advances t and clears
+//                 the graph's loop condition when the decode is done.
 // No float atomics anywhere: every sum has a fixed order, so results do not
 // depend on the launch configuration or on scheduling.
 #include <algorithm>
