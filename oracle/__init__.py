@@ -65,6 +65,7 @@ class RoundLog(C.Structure):
         ("accepted", C.c_int),
         ("updated", C.c_int64),
         ("support", C.c_int64),
+        ("k_prior", C.c_double),
     ]
 
 
@@ -182,7 +183,8 @@ _keep = []
 
 
 def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell=0,
-                max_rounds=0, noiseless_tol=0.0, literal_ei_test=False, mlp_bf16=None, mlp_threshold=0.0):
+                max_rounds=0, noiseless_tol=0.0, literal_ei_test=False, mlp_bf16=None, mlp_threshold=0.0,
+                adaptive_k=False):
     """mlp_bf16: the learned scorer's parameters as a uint16 array of BF16 bit patterns
     (enables the learned rule); None keeps Algorithm 2's analytic rule."""
     ptr = None
@@ -191,7 +193,7 @@ def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell
         _keep.append(arr)
         del _keep[:-8]
         ptr = arr.ctypes.data
-    return Params(sigma_s, sigma_n, int(quantised), 0, c, alpha, ell, max_rounds,
+    return Params(sigma_s, sigma_n, int(quantised), int(adaptive_k), c, alpha, ell, max_rounds,
                   noiseless_tol, int(literal_ei_test), int(mlp_bf16 is not None), ptr, mlp_threshold)
 
 

@@ -304,7 +304,7 @@ typedef struct {
     double sigma_s;       /* signal std (mu = N(0, sigma_s^2))               */
     double sigma_n;       /* noise std  (nu = N(0, sigma_n^2)); 0 = noiseless */
     int quantised;        /* Table "scores": quantised (1) or continuous (0) */
-    int adaptive_k;       /* must be 0 here                                  */
+    int adaptive_k;       /* Alg. 2's adaptive_k flag (analytic scores only) */
     double c;             /* sweep step; 0 = Eq. (finetune_c_*) rule         */
     double alpha;         /* consensus threshold; 0 = floor(d/2)+1           */
     int ell;              /* explicit series terms; 0 = 4                    */
@@ -334,6 +334,7 @@ typedef struct {
     int accepted;
     int64_t updated;       /* columns that received an update                */
     int64_t support;       /* |supp x'| after H_k                            */
+    double k_prior;        /* the sparsity k of the posteriors this round used */
 } orc_round_log;
 
 /* ---- Learned column scorer (not in the paper: an addition whose
@@ -643,14 +644,31 @@ static double orc_stop_level(int64_t m, const orc_params *p, const double *yhat)
     return p->noiseless_tol * l1norm(m, yhat);
 }
 
-/* Alg. 2 (Robust-l0), non-adaptive variants.                                */
+/* Alg. 2's adaptive_k step, after an accepted round: the sparsity left in
+ * the residual, k0 = k - sum_j (1 - p_z(x_hat_j)), floored at m/100; the
+ * posteriors are then rebuilt with rho = k0/m.  reading: the printed
+ * k - sum_j p_z(x_hat_j) would count nearly every one of the n zero entries
+ * (p_z(0) = 1); the sum is of the probability that x_hat_j is nonzero, so
+ * k0 is k less the support found so far, as the text of Section "Adaptive
+ * k" describes (an update leaves a (k-1)-sparse problem).                  */
+double orc_adaptive_k0(int64_t n, int64_t m, int64_t k, const orc_post *P, const double *xhat)
+{
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+        if (xhat[j] != 0.0) s += 1.0 - exp(orc_log_pbreve(&P->pz, xhat[j]));
+    double k0 = (double)k - s;
+    double floor_k = floor((double)m / 100.0);
+    return (k0 > floor_k) ? k0 : floor_k;
+}
+
+/* Alg. 2 (Robust-l0): all four variants of Table "variants".                */
 int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *yhat, int64_t k,
                const orc_params *pin, double *xhat, orc_stats *st,
                orc_round_log *log_out, int log_cap)
 {
     if (n < 1 || m < 1 || d < 1 || d > m || k < 1 || k > n || !rows || !yhat || !xhat || !pin)
         return ORC_EINVAL;
-    if (pin->adaptive_k) return ORC_EINVAL;
+    if (pin->adaptive_k && pin->learned) return ORC_EINVAL;
     orc_params p;
     orc_resolve(pin, d, n, m, k, &p);
     orc_post *PP = (orc_post *)malloc(sizeof(orc_post));
@@ -670,6 +688,7 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
     double l1h = l1norm(m, rh);
     double stop = orc_stop_level(m, &p, yhat);
     int rounds = 0, acc_rounds = 0;
+    double k_prior = (double)k;
     for (int r = 0; r < R; ++r) {
         if (l1h <= stop) break;                           /* converged */
         double t = 1.0 - r * p.c;
@@ -678,11 +697,17 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
         if (rc) break;
         double l1 = l1norm(m, rp);
         int accepted = (l1 < l1h);                        /* strict, as printed */
+        double k_used = k_prior;
         if (accepted) {
             memcpy(xhat, xp, (size_t)n * sizeof(double));
             memcpy(rh, rp, (size_t)m * sizeof(double));
             l1h = l1;
             acc_rounds++;
+            if (p.adaptive_k) {
+                k_prior = orc_adaptive_k0(n, m, k, PP, xhat);
+                rc = orc_post_init(PP, d, k_prior / (double)m, &p);
+                if (rc) break;
+            }
         }
         if (log_out && r < log_cap) {
             int64_t supp = 0;
@@ -693,6 +718,7 @@ int orc_decode(int64_t n, int64_t m, int d, const int32_t *rows, const double *y
             log_out[r].accepted = accepted;
             log_out[r].updated = upd;
             log_out[r].support = supp;
+            log_out[r].k_prior = k_used;
         }
         rounds++;
     }
