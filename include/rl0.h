@@ -54,7 +54,7 @@ typedef struct {
     double sigma_s;        /* std of the nonzeros of x (mu); 0 = 1.0                          */
     double sigma_n;        /* std of the noise (nu); 0 = noiseless                            */
     int    quantised;      /* Table "scores": 1 = quantised scores, 0 = continuous            */
-    int    adaptive_k;     /* the adaptive_k flag of Algorithm 2; must be 0                   */
+    int    adaptive_k;     /* the adaptive_k flag of Algorithm 2 (analytic scorer only)      */
     double c;              /* sweep step of t; 0 = Eqs. (finetune_c_quant)/(finetune_c_cont)  */
     double alpha;          /* consensus threshold on n_e - n_z; 0 = floor(d/2)+1 (quantised)  */
                            /* or d/2 (continuous)                                            */
@@ -122,10 +122,16 @@ void rl0_free_expander(rl0_expander *A);
 int rl0_sketch(const rl0_expander *A, const float *x_dev, double sigma_n, uint64_t noise_seed,
                float *y_dev, void *cuda_stream);
 
-/* Algorithm 2 (Robust-l0), non-adaptive, on one instance.
+/* Algorithm 2 (Robust-l0) on one instance: the four variants of Table
+ * "variants" (params->quantised, params->adaptive_k).
  * y_dev: device float[m]; xhat_dev: device float[n] (output, overwritten).
  * k in [1, n].  params may be NULL (all defaults with sigma_n = 0).
- * stats (host, may be NULL) is filled after the stream is synchronised. */
+ * stats (host, may be NULL) is filled after the stream is synchronised.
+ * adaptive_k (Section "Adaptive k"): after every accepted round the posteriors
+ * are rebuilt for the sparsity left, k0 = k - sum_j (1 - p_z(x_hat_j)) floored
+ * at m/100 (the sum in FP64 over the support in ascending j); H_k keeps k.
+ * The rounds then run one launch group at a time with the host in the loop
+ * (no captured graph).  With scorer = 1 it returns RL0_ERR_UNSUPPORTED. */
 int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
                float *xhat_dev, rl0_stats *stats, void *cuda_stream);
 
@@ -152,7 +158,8 @@ int rl0_round_step(const rl0_expander *A, const float *y_dev, int64_t k, const r
  * xhat_dev and k point to `count` entries each (host arrays of device
  * pointers); params points to `count` entries or is NULL; stats (host) to
  * `count` entries or NULL.  Each instance's result equals what rl0_decode
- * gives for it alone. */
+ * gives for it alone.  The learned scorer and adaptive_k (a host step after
+ * every accepted round) return RL0_ERR_UNSUPPORTED. */
 int rl0_decode_batched(int count, const rl0_expander *const *A, const float *const *y_dev,
                        const int64_t *k, const rl0_params *params, float *const *xhat_dev,
                        rl0_stats *stats, void *cuda_stream);
@@ -173,7 +180,8 @@ int rl0_decode_batched(int count, const rl0_expander *const *A, const float *con
  * loads the library until the process exits.  The caller passes y_dev and
  * xhat_dev as for rl0_decode and gets the same result; the kernels are
  * launched directly on the stream.  Limits: n <= 65536, m <= 32768 (larger
- * instances return RL0_ERR_TOO_LARGE); stats.ms and the profile fields stay 0.
+ * instances return RL0_ERR_TOO_LARGE); adaptive_k returns RL0_ERR_UNSUPPORTED;
+ * stats.ms and the profile fields stay 0.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call reuses the same array and clears the
@@ -194,6 +202,8 @@ typedef struct {
     int    updated;        /* columns that received an update                   */
     int    support;        /* |supp x_hat| after the round                       */
     int    hk_dropped;     /* entries H_k zeroed                                 */
+    double k_prior;        /* the sparsity k of the posteriors the round used
+                              (k, or the adaptive_k prior k0)                    */
 } rl0_round_record;
 
 int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap);

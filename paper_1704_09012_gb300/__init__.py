@@ -69,7 +69,7 @@ class Stats(C.Structure):
 class RoundRecord(C.Structure):
     _fields_ = [
         ("t", C.c_double), ("l1_candidate", C.c_double), ("l1_hat", C.c_double), ("accepted", C.c_int),
-        ("updated", C.c_int), ("support", C.c_int), ("hk_dropped", C.c_int),
+        ("updated", C.c_int), ("support", C.c_int), ("hk_dropped", C.c_int), ("k_prior", C.c_double),
     ]
 
 

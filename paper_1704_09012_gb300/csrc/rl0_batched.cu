@@ -483,7 +483,9 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
     for (int i = 0; i < count; ++i) {
         rc[i] = rl0::resolve(A[i]->n, A[i]->m, A[i]->d, k[i], params ? params + i : nullptr, &R[i]);
         if (rc[i]) return rc[i];
-        if (R[i].p.scorer == 1) return RL0_ERR_UNSUPPORTED;
+        // the learned scorer and adaptive_k (a host step after every accepted
+        // round) do not fit one persistent launch
+        if (R[i].p.scorer == 1 || R[i].p.adaptive_k) return RL0_ERR_UNSUPPORTED;
         thr_off[i + 1] = thr_off[i] + R[i].nrounds;
     }
     std::lock_guard<std::mutex> lock(g_buf_mutex);

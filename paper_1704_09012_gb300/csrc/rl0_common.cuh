@@ -186,8 +186,11 @@ float series_threshold_down(const HostSeries &H, double T);
 Series to_device_series(const HostSeries &H);
 double default_c(int quantised, double delta, double rho);
 int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolved *R);
-void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr);
-void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out);
+// k_prior > 0: the posteriors use sparsity k_prior instead of k (adaptive_k)
+void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr,
+                 double k_prior = 0.0);
+void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out, double k_prior = 0.0);
+double adaptive_k0(int64_t m, int d, int64_t k, const Resolved &R, double k_prior, const float *vals, int64_t count);
 }  // namespace rl0
 
 // ---- helpers shared by translation units -------------------------------

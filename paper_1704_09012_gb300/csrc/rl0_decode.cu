@@ -554,6 +554,19 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
     }
 }
 
+// (column, FP32 bits of x_hat) of every support entry, for the host's
+// adaptive_k step.
+__global__ void k_support_pairs(KArgs a, int *out)
+{
+    const unsigned cnt = a.st->shat_count;
+    const float *x = a.ctx->x;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int j = a.list[e];
+        out[2 * (size_t)e] = j;
+        out[2 * (size_t)e + 1] = __float_as_int(x[j]);
+    }
+}
+
 // Features of every learned-scorer candidate of one round (for training logs):
 // feat[e*16..], meta[e*4..] = (column, slot, analytic pass, l1 test), omega[e].
 template <int DMAX, bool IND>
@@ -808,6 +821,7 @@ struct HostStage {
     DecodeState st;
     RoundThr thr[RL0_MAX_ROUNDS];
     RoundLog log[RL0_MAX_ROUNDS];
+    double kprior[RL0_MAX_ROUNDS];     // the posteriors' sparsity per round (adaptive_k)
 };
 
 // Host tables of the last parameter set, reused when a decode repeats it.
@@ -951,6 +965,109 @@ static void cached_pz(rl0_expander *A, int64_t k, const Resolved &R, float *out)
     }
 }
 
+// Alg. 2 with the adaptive_k flag: the rounds of the captured graph, launched
+// one round at a time; after each accepted round the host reads the support,
+// takes the adaptive_k step in FP64 (ascending column order) and uploads the
+// rebuilt posteriors and thresholds before the next round.
+static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const Resolved &R, float *xhat_dev,
+                           rl0_stats *stats, cudaStream_t s)
+{
+    HostStage *H = (HostStage *)A->host_pinned;
+    const Workspace &w = A->ws;
+    const KArgs a = make_args(A);
+    const int dmax = dmax_of(A->d);
+    cudaEvent_t *ev = (cudaEvent_t *)A->events;
+    if (stats) CK(cudaEventRecord(ev[0], s));
+    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
+    k_start<<<1, 32, 0, s>>>(a, 0, 0);
+    CK(cudaGetLastError());
+    // the device set the stop level (noiseless: tol ||y_hat||_1); keep it
+    CK(cudaMemcpyAsync(&H->ctx, w.ctx, sizeof(DecodeCtx), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double stop_level = H->ctx.stop_level;
+    double kprior = (double)k;
+    int accepted = H->st.accepted_rounds;
+    std::vector<int> pairs;
+    std::vector<std::pair<int, float>> supp;
+    std::vector<float> vals;
+    int launches = 3;
+    for (int r = 0; r < R.nrounds && !H->st.done; ++r) {
+        H->kprior[r] = kprior;
+        launch_round(a, dmax, R.indicator, 0, s);
+        launches += 3;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (H->st.status) break;
+        if (H->st.accepted_rounds == accepted) continue;
+        accepted = H->st.accepted_rounds;
+        if (H->st.done) break;
+        // the adaptive_k step on the accepted x_hat
+        const unsigned cnt = H->st.shat_count;
+        pairs.resize(2 * (size_t)cnt);
+        if (cnt) {
+            k_support_pairs<<<2 * a.nsm, 256, 0, s>>>(a, a.res_list);
+            launches += 1;
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(pairs.data(), a.res_list, 2 * (size_t)cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        supp.resize(cnt);
+        for (unsigned e = 0; e < cnt; ++e) {
+            float v;
+            std::memcpy(&v, &pairs[2 * (size_t)e + 1], sizeof(float));
+            supp[e] = std::make_pair(pairs[2 * (size_t)e], v);
+        }
+        std::sort(supp.begin(), supp.end());
+        vals.resize(cnt);
+        for (unsigned e = 0; e < cnt; ++e) vals[e] = supp[e].second;
+        kprior = rl0::adaptive_k0(A->m, A->d, k, R, kprior, vals.data(), (int64_t)cnt);
+        rl0::fill_tables(A->m, A->d, k, R, &H->ctx, H->thr, R.nrounds, kprior);
+        H->ctx.y = y_dev;
+        H->ctx.x = xhat_dev;
+        H->ctx.want_log = 1;
+        H->ctx.passed = nullptr;
+        H->ctx.stop_level = stop_level;
+        CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+        if (!R.indicator) {
+            rl0::pz_lower_bounds(A->m, A->d, k, R, H->pzlb, kprior);
+            CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
+        }
+    }
+    k_final_sum<<<1, 32, 0, s>>>(a);
+    launches += 1;
+    CK(cudaGetLastError());
+    if (stats) CK(cudaEventRecord(ev[1], s));
+    CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(H->log, w.rlog, R.nrounds * sizeof(RoundLog), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // the next decode on this expander starts from the cached (non-adaptive) tables
+    TableCache *tc = (TableCache *)A->table_cache;
+    if (tc) tc->valid = false;
+    if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    A->last_log_rounds = H->st.rounds_run;
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        std::memset(stats, 0, sizeof(*stats));
+        stats->rounds = H->st.rounds_run;
+        stats->accepted_rounds = H->st.accepted_rounds;
+        stats->converged = H->st.converged;
+        stats->status = H->st.status;
+        stats->support_size = H->st.nnz;
+        stats->final_l1 = H->st.final_l1;
+        stats->ms = ms;
+        stats->hk_rounds = H->st.hk_rounds;
+        stats->fallback_rounds = H->st.fallback_rounds;
+        stats->launches = launches;
+    }
+    if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
+    return RL0_OK;
+}
+
 static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
                          float *xhat_dev, rl0_stats *stats, cudaStream_t s)
 {
@@ -972,6 +1089,8 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
     }
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+    if (R.p.adaptive_k) return decode_adaptive(A, y_dev, k, R, xhat_dev, stats, s);
+    for (int r = 0; r < R.nrounds; ++r) H->kprior[r] = (double)k;
     const int dmax = dmax_of(A->d);
     GraphCache *gc = (GraphCache *)A->graph_cache;
     const int prof = R.p.profile ? 1 : 0;
@@ -1091,6 +1210,7 @@ extern "C" int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int 
         out[r].updated = H->log[r].updated;
         out[r].support = H->log[r].support;
         out[r].hk_dropped = H->log[r].hk_dropped;
+        out[r].k_prior = H->kprior[r];
     }
     return A->last_log_rounds;
 }
@@ -1272,6 +1392,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     Resolved R;
     rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
+    if (R.p.adaptive_k) return RL0_ERR_UNSUPPORTED;
     unsigned char *base = nullptr;
     rc = static_scratch_base(A->device, &base);
     if (rc) return rc;

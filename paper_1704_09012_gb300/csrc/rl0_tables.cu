@@ -214,7 +214,8 @@ int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolv
     if (p.sigma_s == 0.0) p.sigma_s = 1.0;
     if (!(p.sigma_s > 0.0) || !(p.sigma_n >= 0.0) || !std::isfinite(p.sigma_n) || !std::isfinite(p.sigma_s))
         return RL0_ERR_INVALID_ARG;
-    if (p.adaptive_k) return RL0_ERR_UNSUPPORTED;
+    if (p.adaptive_k != 0 && p.adaptive_k != 1) return RL0_ERR_INVALID_ARG;
+    if (p.adaptive_k && p.scorer != 0) return RL0_ERR_UNSUPPORTED;
     if (k < 1 || k > n) return RL0_ERR_INVALID_ARG;
     if (p.c == 0.0) p.c = default_c(p.quantised, (double)m / (double)n, (double)k / (double)m);
     if (!(p.c > 0.0 && p.c <= 1.0)) return RL0_ERR_INVALID_ARG;
@@ -248,10 +249,12 @@ int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolv
 }
 
 // The decode context (minus the data pointers) and the per-round thresholds.
-void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr)
+void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr, int nthr,
+                 double k_prior)
 {
     const rl0_params &p = R.p;
-    const double rho = (double)k / (double)m;
+    // the posteriors' sparsity: k, or the adaptive_k prior k0 (Alg. 2)
+    const double rho = (k_prior > 0.0 ? k_prior : (double)k) / (double)m;
     const double s2 = p.sigma_s * p.sigma_s, n2 = p.sigma_n * p.sigma_n;
     std::memset(ctx, 0, sizeof(*ctx));
     ctx->k = k;
@@ -319,20 +322,43 @@ static double half_bits_value(unsigned h)
 // bin c = b >> RL0_PZ_SHIFT the posterior is at least p_breve_z at the
 // FP16 value of (c + 1) << RL0_PZ_SHIFT.  The factor 1 - 1e-5 covers the FP32
 // evaluation on the device; past the series cut the device takes 0.
-void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out)
+void pz_lower_bounds(int64_t m, int d, int64_t k, const Resolved &R, float *out, double k_prior)
 {
     const rl0_params &p = R.p;
     if (!(p.sigma_n > 0.0)) {
         for (int c = 0; c < RL0_PZ_BINS; ++c) out[c] = 0.0f;
         return;
     }
-    const double rho = (double)k / (double)m;
+    const double rho = (k_prior > 0.0 ? k_prior : (double)k) / (double)m;
     const HostSeries hz = make_series(d * rho, p.sigma_s * p.sigma_s, p.sigma_n * p.sigma_n, p.ell);
     const double cut = (double)to_device_series(hz).cut;
     for (int c = 0; c < RL0_PZ_BINS; ++c) {
         const double U = half_bits_value((unsigned)(c + 1) << RL0_PZ_SHIFT);
         out[c] = (U > cut) ? 0.0f : (float)((1.0 - 1e-5) / series_F(hz, U));
     }
+}
+
+// Alg. 2's adaptive_k step from the support of x_hat (index, value pairs in
+// ascending index): k0 = k - sum_j (1 - p_z(x_hat_j)) in FP64, floored at
+// m/100, with p_z the posterior at the prior k_prior (reading: the printed
+// k - sum_j p_z(x_hat_j) would count almost every zero entry).
+double adaptive_k0(int64_t m, int d, int64_t k, const Resolved &R, double k_prior, const float *vals, int64_t count)
+{
+    const rl0_params &p = R.p;
+    double s = 0.0;
+    if (p.sigma_n > 0.0) {
+        const double rho = k_prior / (double)m;
+        const HostSeries hz = make_series(d * rho, p.sigma_s * p.sigma_s, p.sigma_n * p.sigma_n, p.ell);
+        for (int64_t e = 0; e < count; ++e)
+            if (vals[e] != 0.0f) s += 1.0 - 1.0 / series_F(hz, (double)vals[e]);
+    } else {
+        // noiseless: p_z is the indicator of |w| <= tol
+        for (int64_t e = 0; e < count; ++e)
+            if (std::fabs((double)vals[e]) > p.noiseless_tol) s += 1.0;
+    }
+    const double k0 = (double)k - s;
+    const double lo = std::floor((double)m / 100.0);
+    return k0 > lo ? k0 : lo;
 }
 
 }  // namespace rl0

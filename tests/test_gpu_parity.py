@@ -235,9 +235,6 @@ def test_decode_edge_cases(rl0):
     with pytest.raises(rl0.Rl0Error) as e:
         rl0.decode(A, _cuda(bad), I.k, sigma_n=1e-3)
     assert e.value.code == -7
-    with pytest.raises(rl0.Rl0Error) as e:
-        rl0.decode(A, _cuda(y32), I.k, sigma_n=1e-3, adaptive_k=True)
-    assert e.value.code == -5
 
 
 def test_decode_is_deterministic_and_host_api_agrees(rl0):
