@@ -253,6 +253,32 @@ def bench_learned(rl0, torch, flush, train_instances=4, eval_instances=2):
     return res
 
 
+def bench_adaptive(rl0, torch, A, y_dev, x, k, params, flush, steps):
+    """The adaptive_k variant of the same decode (Table "variants"): its rounds run one
+    at a time with the host's adaptive_k step after every accepted round, so it is
+    timed on the device stream around the whole call, L2 flushed in between."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    p = dict(params, adaptive_k=True)
+    rl0.decode(A, y_dev, k, **p)
+    ms, st = [], None
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xh, st = rl0.decode(A, y_dev, k, **p)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    xr = xh.cpu().numpy().astype(np.float64)
+    t = float(np.mean(ms))
+    nnz = A.n * A.d
+    return {"workload": "same instance, adaptive_k=1 (Robust-l0-adaptive%s)" % ("-quantised" if params.get("quantised") else ""),
+            "ms_to_recover": t, "rounds": st["rounds"], "accepted_rounds": st["accepted_rounds"],
+            "converged": st["converged"], "rel_l1_err": float(np.abs(xr - x).sum() / np.abs(x).sum()),
+            "value": nnz * st["rounds"] / (t * 1e-3), "unit": UNIT, "launches": st["launches"]}
+
+
 def cpu_baseline(cfg, seed, budget_s=20.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample: full-size rounds
     from the start of the decode (x_hat = 0) until the time budget is spent."""
@@ -330,6 +356,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=4096, help="instances of the batched sub-measurement (0: skip)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-scorer sub-measurement")
+    ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive_k sub-measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -455,6 +482,8 @@ def main():
     }
     if args.batched > 0:
         line["batched"] = bench_batched(rl0, torch, args.batched, max(1, min(args.steps, 3)), flush)
+    if not args.no_adaptive:
+        line["adaptive"] = bench_adaptive(rl0, torch, A, y_dev, x, k, params, flush, max(1, min(args.steps, 3)))
     if not args.no_learned:
         line["learned"] = bench_learned(rl0, torch, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
