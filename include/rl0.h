@@ -135,6 +135,22 @@ int rl0_sketch(const rl0_expander *A, const float *x_dev, double sigma_n, uint64
 int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
                float *xhat_dev, rl0_stats *stats, void *cuda_stream);
 
+/* Algorithm 1 (Parallel-l0) on one instance of the noiseless model y = A x:
+ * from x_hat = 0, every iteration gives each column j the last anchor r_i != 0
+ * in row order with n_e - n_z >= alpha, n_e = #{l in N(j): r_l = r_i},
+ * n_z = #{l in N(j): r_l = 0}; then x_hat += u and r = y - A x_hat.  Equality
+ * and zero are |.| <= tol on the FP32 residuals.  It stops when an iteration
+ * changes nothing; stats.converged = 1 when then every |r_i| <= tol, and
+ * stats.accepted_rounds counts the iterations that changed x_hat.
+ * It runs the round kernels of rl0_decode with the 0/1 scores, no H_k and no
+ * acceptance test.  alpha: 0 gives floor(d/2) + 1; alpha < d/2 returns
+ * RL0_ERR_UNSUPPORTED (the kernels apply the l1 test of Alg. 2, which
+ * n_e - n_z >= alpha implies when alpha >= d/2).  tol: 0 gives 1e-5 (FP32
+ * residuals carry rounding of about 1e-7 |y|).  max_iter: 0 gives 100, at
+ * most 1024.  y_dev: device float[m]; xhat_dev: device float[n] (output). */
+int rl0_parallel_l0(const rl0_expander *A, const float *y_dev, double alpha, double tol, int max_iter,
+                    float *xhat_dev, rl0_stats *stats, void *cuda_stream);
+
 /* rl0_decode with host buffers: copies y_host (float[m]) to the device and
  * x_hat back to xhat_host (float[n]) on the stream.  Pinned host memory gives
  * asynchronous copies; pageable memory works too. */

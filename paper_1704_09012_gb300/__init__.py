@@ -30,7 +30,7 @@ ERRORS = {
 EXPORTS = [
     "rl0_make_expander", "rl0_expander_from_rows", "rl0_expander_rows", "rl0_expander_shape",
     "rl0_free_expander", "rl0_sketch", "rl0_decode", "rl0_decode_host", "rl0_round_step",
-    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static",
+    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static", "rl0_parallel_l0",
     "rl0_candidate_features", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
     "rl0_mlp_forward", "rl0_mlp_params",
 ]
@@ -99,6 +99,7 @@ def _lib():
                                          C.POINTER(vp), vp, vp]
         L.rl0_decode_log.argtypes = [vp, C.POINTER(RoundRecord), i32]
         L.rl0_decode_static.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.POINTER(Stats), vp]
+        L.rl0_parallel_l0.argtypes = [vp, vp, C.c_double, C.c_double, i32, vp, C.POINTER(Stats), vp]
         L.rl0_candidate_features.argtypes = [vp, vp, i64, C.POINTER(Params), i32, vp, vp, vp, vp, vp, i32,
                                              C.POINTER(i32), vp]
         L.rl0_mlp_init.argtypes = [C.c_uint64, vp, vp]
@@ -218,6 +219,17 @@ def decode_static(A, y, k, out=None, stream=None, **params):
     _check(_lib().rl0_decode_static(A.handle, _dev(y, torch.float32, A.m, "y"), int(k), C.byref(p),
                                     _dev(x, torch.float32, A.n, "x_hat"), C.byref(st), _stream(stream)),
            "rl0_decode_static")
+    return x, st.as_dict()
+
+
+def parallel_l0(A, y, alpha=0.0, tol=0.0, max_iter=0, out=None, stream=None):
+    """Algorithm 1 (Parallel-l0) on the noiseless model y = A x.  Returns (x_hat CUDA
+    float32 [n], stats dict); stats["accepted_rounds"] counts the iterations."""
+    x = out if out is not None else torch.empty(A.n, dtype=torch.float32, device="cuda")
+    st = Stats()
+    _check(_lib().rl0_parallel_l0(A.handle, _dev(y, torch.float32, A.m, "y"), float(alpha), float(tol),
+                                  int(max_iter), _dev(x, torch.float32, A.n, "x_hat"), C.byref(st),
+                                  _stream(stream)), "rl0_parallel_l0")
     return x, st.as_dict()
 
 

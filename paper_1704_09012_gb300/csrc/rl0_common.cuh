@@ -79,6 +79,8 @@ struct DecodeState {
     unsigned iters;           // accept invocations (bounds the graph's while loop)
     unsigned col_done;        // CTAs of the column kernel finished (last one applies H_k)
     unsigned rb_done;         // CTAs of the rebuild finished (last one accepts or undoes)
+    unsigned big_hat;         // Alg. 1 mode: rows of r_hat with |r_i| > conv_tol
+    unsigned big_cand;        // Alg. 1 mode: the same count for the candidate r
     int rounds_run;
     int accepted_rounds;
     int hk_rounds;
@@ -113,6 +115,8 @@ struct DecodeCtx {
     int32_t *passed;          // optional per-column pass flags (round_step)
     int want_log;
     int no_accept;            // round_step: stop after the rebuild (no accept, no undo)
+    int always_accept;        // Alg. 1 (Parallel-l0): keep every iteration, stop when one changes nothing
+    float conv_tol;           // Alg. 1: converged when every |r_i| <= conv_tol (0: Alg. 2's stop level)
 };
 
 struct UndoEntry {

@@ -64,6 +64,10 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
         // r = y_hat with x_hat = 0: the FP64 residual-norm partial is the same sum
         if (!src_override) a.final_part[(size_t)dst * a.nchunks + blockIdx.x] = s;
     }
+    if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows not yet zero
+        const int big = __syncthreads_count(i < a.m && !(fabsf(src[i < a.m ? i : 0]) <= ctx->conv_tol));
+        if (threadIdx.x == 0 && big) atomicAdd(&a.st->big_hat, (unsigned)big);
+    }
 }
 
 // Zero the working x.
@@ -96,7 +100,7 @@ __global__ void k_start(KArgs a, int round0, int empty_support)
     double stop = a.ctx->stop_level;
     if (a.ctx->stop_rel > 0.0) stop = a.ctx->stop_rel * l1;
     a.ctx->stop_level = stop;
-    st->converged = (l1 <= stop);
+    st->converged = (a.ctx->conv_tol > 0.0f) ? (st->big_hat == 0) : (l1 <= stop);
     st->done = (status != 0) || st->converged || (round0 >= a.ctx->nrounds);
     st->nnz = st->shat_count;
     st->nnz_delta = 0;
@@ -359,7 +363,7 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
             double v = 0.0;
             for (int c = t; c < a.nchunks; c += 32) v += __ldcg(a.l1part + c);
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (t == 0) { s_l1 = v; s_acc = (v < st->l1_hat); }
+            if (t == 0) { s_l1 = v; s_acc = ctx->always_accept ? 1 : (v < st->l1_hat); }
         }
         __syncthreads();
         if (s_acc) {
@@ -429,7 +433,15 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
         st->rounds_run += 1;
         st->iters += 1;
         st->l1_new = l1n;
-        st->converged = (st->l1_hat <= ctx->stop_level);
+        if (ctx->always_accept) {
+            // Alg. 1: every iteration is kept; it ends when one changes nothing
+            if (upd > 0) st->big_hat = __ldcg(&st->big_cand);
+            st->converged = (st->big_hat == 0);
+            if (upd == 0) st->done = 1;
+        } else {
+            st->converged = (st->l1_hat <= ctx->stop_level);
+        }
+        st->big_cand = 0;
         if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds || st->status != 0)
             st->done = 1;
         if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
@@ -495,6 +507,10 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     if (threadIdx.x == 0) {
         a.l1part[blockIdx.x] = s2.x;
         a.final_part[(size_t)(st->cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
+    }
+    if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows of r' not yet zero
+        const int big = __syncthreads_count(i < a.m && !(fabs(l1) <= (double)ctx->conv_tol));
+        if (threadIdx.x == 0 && big) atomicAdd(&st->big_cand, (unsigned)big);
     }
     if (no_accept) return;
     // ---- the launch's last CTA accepts or undoes the round
@@ -965,6 +981,27 @@ static void cached_pz(rl0_expander *A, int64_t k, const Resolved &R, float *out)
     }
 }
 
+// The captured round loop for this shape (captured on first use).
+static int get_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int prof, int learned, GraphEntry **out)
+{
+    GraphCache *gc = (GraphCache *)A->graph_cache;
+    for (auto &g : gc->entries)
+        if (g.nrounds == nrounds && g.dmax == dmax && g.indicator == indicator && g.profile == prof &&
+            g.learned == learned) {
+            *out = &g;
+            return RL0_OK;
+        }
+    GraphEntry fresh;
+    const int rc = capture_decode_graph(A, nrounds, dmax, indicator, prof, learned, &fresh);
+    if (rc) {
+        for (auto ev : fresh.events) if (ev) cudaEventDestroy(ev);
+        return rc;
+    }
+    gc->entries.push_back(fresh);
+    *out = &gc->entries.back();
+    return RL0_OK;
+}
+
 // Alg. 2 with the adaptive_k flag: the rounds of the captured graph, launched
 // one round at a time; after each accepted round the host reads the support,
 // takes the adaptive_k step in FP64 (ascending column order) and uploads the
@@ -1092,24 +1129,11 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     if (R.p.adaptive_k) return decode_adaptive(A, y_dev, k, R, xhat_dev, stats, s);
     for (int r = 0; r < R.nrounds; ++r) H->kprior[r] = (double)k;
     const int dmax = dmax_of(A->d);
-    GraphCache *gc = (GraphCache *)A->graph_cache;
     const int prof = R.p.profile ? 1 : 0;
     const int learned = R.p.scorer == 1;
     GraphEntry *E = nullptr;
-    for (auto &g : gc->entries)
-        if (g.nrounds == R.nrounds && g.dmax == dmax && g.indicator == R.indicator && g.profile == prof &&
-            g.learned == learned)
-            E = &g;
-    if (!E) {
-        GraphEntry fresh;
-        rc = capture_decode_graph(A, R.nrounds, dmax, R.indicator, prof, learned, &fresh);
-        if (rc) {
-            for (auto ev : fresh.events) if (ev) cudaEventDestroy(ev);
-            return rc;
-        }
-        gc->entries.push_back(fresh);
-        E = &gc->entries.back();
-    }
+    rc = get_graph(A, R.nrounds, dmax, R.indicator, prof, learned, &E);
+    if (rc) return rc;
     cudaEvent_t *ev = (cudaEvent_t *)A->events;
     if (stats) CK(cudaEventRecord(ev[0], s));
     CK(cudaGraphLaunch(E->exec, s));
@@ -1246,6 +1270,82 @@ extern "C" int rl0_decode_host(const rl0_expander *A, const float *y_host, int64
     cudaFreeAsync(yd, s);
     cudaFreeAsync(xd, s);
     return rc;
+}
+
+extern "C" int rl0_parallel_l0(const rl0_expander *Ac, const float *y_dev, double alpha, double tol, int max_iter,
+                               float *xhat_dev, rl0_stats *stats, void *cuda_stream)
+{
+    rl0_expander *A = const_cast<rl0_expander *>(Ac);
+    if (!A || !y_dev || !xhat_dev) return RL0_ERR_INVALID_ARG;
+    if (alpha == 0.0) alpha = (double)(A->d / 2 + 1);
+    if (!(alpha <= (double)A->d) || !(tol >= 0.0) || max_iter < 0 || max_iter > RL0_MAX_ROUNDS)
+        return RL0_ERR_INVALID_ARG;
+    // the kernels keep Alg. 2's l1 test: alpha >= d/2 implies it (n_e > d/2
+    // rows move to zero, at most d - n_e rows grow, each by at most |omega|)
+    if (alpha < 0.5 * A->d) return RL0_ERR_UNSUPPORTED;
+    if (tol == 0.0) tol = 1e-5;
+    if (max_iter == 0) max_iter = 100;
+    int rc = rl0_set_device_of(A);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rl0_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.sigma_s = 1.0;
+    p.quantised = 1;                               // 0/1 scores: q_e = 1{|D| <= tol}, q_z = 1{|r| <= tol}
+    p.alpha = alpha;
+    p.noiseless_tol = tol;
+    p.c = 0.5;
+    Resolved R;
+    rc = rl0::resolve(A->n, A->m, A->d, A->n, &p, &R);
+    if (rc) return rc;
+    R.nrounds = max_iter;
+    R.stop_level = -1.0;
+    R.stop_rel = 0.0;
+    HostStage *H = (HostStage *)A->host_pinned;
+    rl0::fill_tables(A->m, A->d, A->n, R, &H->ctx, H->thr, 2);
+    for (int r = 0; r < max_iter; ++r) {           // every iteration takes the t in (0, 1) thresholds
+        H->thr[r] = H->thr[1];
+        H->kprior[r] = (double)A->n;
+    }
+    H->ctx.y = y_dev;
+    H->ctx.x = xhat_dev;
+    H->ctx.want_log = 1;
+    H->ctx.passed = nullptr;
+    H->ctx.always_accept = 1;
+    H->ctx.conv_tol = (float)tol;
+    const Workspace &w = A->ws;
+    CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.thr, H->thr, max_iter * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
+    TableCache *tc = (TableCache *)A->table_cache;
+    if (tc) tc->valid = false;                     // H->ctx no longer holds a decode's cached tables
+    GraphEntry *E = nullptr;
+    rc = get_graph(A, max_iter, dmax_of(A->d), 1, 0, 0, &E);
+    if (rc) return rc;
+    cudaEvent_t *ev = (cudaEvent_t *)A->events;
+    if (stats) CK(cudaEventRecord(ev[0], s));
+    CK(cudaGraphLaunch(E->exec, s));
+    if (stats) CK(cudaEventRecord(ev[1], s));
+    CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(H->log, w.rlog, max_iter * sizeof(RoundLog), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    A->last_log_rounds = H->st.rounds_run;
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        std::memset(stats, 0, sizeof(*stats));
+        stats->rounds = H->st.rounds_run;
+        stats->accepted_rounds = H->st.accepted_rounds;
+        stats->converged = H->st.converged;
+        stats->status = H->st.status;
+        stats->support_size = H->st.nnz;
+        stats->final_l1 = H->st.final_l1;
+        stats->ms = ms;
+        stats->launches = launches_per_decode(H->st.rounds_run);
+    }
+    if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
+    return RL0_OK;
 }
 
 __global__ void k_copy_f(const float *src, float *dst, int n)

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _header_functions():
     txt = open(os.path.join(ROOT, "include", "rl0.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rl0_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rl0_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
