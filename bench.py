@@ -279,6 +279,24 @@ def bench_adaptive(rl0, torch, A, y_dev, x, k, params, flush, steps):
             "value": nnz * st["rounds"] / (t * 1e-3), "unit": UNIT, "launches": st["launches"]}
 
 
+def bench_parallel_l0(rl0, torch, A, x_dev, x, flush, steps):
+    """Alg. 1 (Parallel-l0) on the noiseless sketch of the bench signal, same expander."""
+    import numpy as np
+    y0 = rl0.sketch(A, x_dev, sigma_n=0.0, noise_seed=0)
+    rl0.parallel_l0(A, y0)
+    ms, st = [], None
+    for _ in range(steps):
+        flush.zero_()
+        xh, st = rl0.parallel_l0(A, y0)
+        ms.append(st["ms"])
+    xr = xh.cpu().numpy().astype(np.float64)
+    t = float(np.mean(ms))
+    return {"workload": "same expander and signal, noiseless y = A x, tol 1e-5, alpha = floor(d/2)+1",
+            "ms_to_recover": t, "iterations": st["accepted_rounds"], "converged": st["converged"],
+            "max_abs_err": float(np.abs(xr - x).max()),
+            "value": A.n * A.d * st["rounds"] / (t * 1e-3), "unit": UNIT}
+
+
 def cpu_baseline(cfg, seed, budget_s=20.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample: full-size rounds
     from the start of the decode (x_hat = 0) until the time budget is spent."""
@@ -484,6 +502,7 @@ def main():
         line["batched"] = bench_batched(rl0, torch, args.batched, max(1, min(args.steps, 3)), flush)
     if not args.no_adaptive:
         line["adaptive"] = bench_adaptive(rl0, torch, A, y_dev, x, k, params, flush, max(1, min(args.steps, 3)))
+        line["parallel_l0"] = bench_parallel_l0(rl0, torch, A, x_dev, x, flush, max(1, min(args.steps, 3)))
     if not args.no_learned:
         line["learned"] = bench_learned(rl0, torch, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
