@@ -151,6 +151,21 @@ int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_p
 int rl0_parallel_l0(const rl0_expander *A, const float *y_dev, double alpha, double tol, int max_iter,
                     float *xhat_dev, rl0_stats *stats, void *cuda_stream);
 
+/* Monte-Carlo check of the posteriors (Section "Comparison with empirical
+ * probabilities", Fig. 3) with the decoder's own FP32 series for sparsity k
+ * (rho = k/m), sigma_s, sigma_n > 0 and ell = 4.  y0_dev: the noiseless sketch
+ * A x (device float[m]); yhat_dev: the noisy one, A x + eta.  nbins <= 1024.
+ *  - rows: for every i with |yhat_i| < wz_max, bin b = floor(|yhat_i| nbins / wz_max);
+ *    hz[3b] += 1, hz[3b+1] += [y0_i == 0], hz[3b+2] += round(2^32 p_breve_z(yhat_i));
+ *  - row pairs: for every column j and rows s < l of N(j) with
+ *    |D| = |yhat_s - yhat_l| < we_max, the same into he with [y0_s == y0_l] and
+ *    p_breve_e(D).
+ * hz_dev, he_dev: device uint64[3 nbins], accumulated into (not cleared), so
+ * several instances add up.  The counts are exact integers. */
+int rl0_posterior_mc(const rl0_expander *A, const float *y0_dev, const float *yhat_dev, int64_t k,
+                     double sigma_s, double sigma_n, int nbins, double wz_max, double we_max,
+                     uint64_t *hz_dev, uint64_t *he_dev, void *cuda_stream);
+
 /* rl0_decode with host buffers: copies y_host (float[m]) to the device and
  * x_hat back to xhat_host (float[n]) on the stream.  Pinned host memory gives
  * asynchronous copies; pageable memory works too. */

@@ -31,6 +31,7 @@ EXPORTS = [
     "rl0_make_expander", "rl0_expander_from_rows", "rl0_expander_rows", "rl0_expander_shape",
     "rl0_free_expander", "rl0_sketch", "rl0_decode", "rl0_decode_host", "rl0_round_step",
     "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static", "rl0_parallel_l0",
+    "rl0_posterior_mc",
     "rl0_candidate_features", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
     "rl0_mlp_forward", "rl0_mlp_params",
 ]
@@ -100,6 +101,8 @@ def _lib():
         L.rl0_decode_log.argtypes = [vp, C.POINTER(RoundRecord), i32]
         L.rl0_decode_static.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.POINTER(Stats), vp]
         L.rl0_parallel_l0.argtypes = [vp, vp, C.c_double, C.c_double, i32, vp, C.POINTER(Stats), vp]
+        L.rl0_posterior_mc.argtypes = [vp, vp, vp, i64, C.c_double, C.c_double, i32, C.c_double, C.c_double,
+                                       vp, vp, vp]
         L.rl0_candidate_features.argtypes = [vp, vp, i64, C.POINTER(Params), i32, vp, vp, vp, vp, vp, i32,
                                              C.POINTER(i32), vp]
         L.rl0_mlp_init.argtypes = [C.c_uint64, vp, vp]
@@ -231,6 +234,25 @@ def parallel_l0(A, y, alpha=0.0, tol=0.0, max_iter=0, out=None, stream=None):
                                   int(max_iter), _dev(x, torch.float32, A.n, "x_hat"), C.byref(st),
                                   _stream(stream)), "rl0_parallel_l0")
     return x, st.as_dict()
+
+
+def posterior_mc(A, y0, yhat, k, sigma_n, sigma_s=1.0, nbins=64, wz_max=None, we_max=None, hz=None, he=None,
+                 stream=None):
+    """Binned Monte-Carlo counts of the posteriors (rl0_posterior_mc).  Returns the CUDA
+    int64 [nbins, 3] histograms (samples, events, sum of 2^32 p_breve) for p_z (rows) and
+    p_e (row pairs of each column); pass hz/he to accumulate over instances."""
+    wz_max = 8.0 * sigma_n if wz_max is None else wz_max
+    we_max = 8.0 * 2 ** 0.5 * sigma_n if we_max is None else we_max
+    if hz is None:
+        hz = torch.zeros((nbins, 3), dtype=torch.int64, device="cuda")
+    if he is None:
+        he = torch.zeros((nbins, 3), dtype=torch.int64, device="cuda")
+    assert hz.shape == (nbins, 3) and he.shape == (nbins, 3) and hz.is_contiguous() and he.is_contiguous()
+    _check(_lib().rl0_posterior_mc(A.handle, _dev(y0, torch.float32, A.m, "y0"), _dev(yhat, torch.float32, A.m, "yhat"),
+                                   int(k), float(sigma_s), float(sigma_n), int(nbins), float(wz_max), float(we_max),
+                                   C.c_void_p(hz.data_ptr()), C.c_void_p(he.data_ptr()), _stream(stream)),
+           "rl0_posterior_mc")
+    return hz, he
 
 
 def decode_host(A, y_host, k, out=None, stream=None, **params):

@@ -18,7 +18,8 @@ LIB = os.path.join(OUT, "librl0.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["rl0_expander.cu", "rl0_decode.cu", "rl0_column_res.cu", "rl0_tables.cu", "rl0_batched.cu", "rl0_mlp.cu"]
+SOURCES = ["rl0_expander.cu", "rl0_decode.cu", "rl0_column_res.cu", "rl0_tables.cu", "rl0_batched.cu", "rl0_mlp.cu",
+           "rl0_mc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]

@@ -5,7 +5,9 @@ For a (delta, sigma, n) cell, rho starts at rho_step and grows by rho_step while
 one of `problems` instances of the generating model GM(n, delta n, rho delta n, d, N(0,1),
 N(0, sigma^2)) (Def. "Generating model") is recovered; an instance counts as recovered
 under Eq. (success_condition_clip) with C_1 = 1.  rho* is the largest rho at which at
-least half of the instances are recovered.  Timings are the decode's own (rl0_stats.ms).
+least half of the instances are recovered; a logistic fit of the recovery data gives the
+50% point and the transition's width (fit_logistic).  Timings are the decode's own
+(rl0_stats.ms).
 
     python -m paper_1704_09012_gb300.phase --delta 0.001 --sigma 0.001 --log2n 22
 
@@ -26,6 +28,36 @@ def success(x_hat, x, m, sigma):
     xl1 = float(np.abs(x).sum())
     tol = min((m * sigma * math.sqrt(2 / math.pi) + math.sqrt(m * sigma * sigma * (1 - 2 / math.pi))) / xl1, 0.1)
     return float(np.abs(x_hat - x).sum()) / xl1 <= tol
+
+
+def fit_logistic(rhos, recovered, problems):
+    """The recovery data fitted with a logistic function (Section "Phase transitions and
+    runtime", after Blanchard et al.): P(recovered | rho) = 1 / (1 + exp((rho - rho50) / w)),
+    fitted by binomial maximum likelihood, w >= 1e-4.  Returns (rho50, w, width) with
+    width = 2 ln(9) w, the distance in rho from 90% to 10% recovery (reading: the paper's
+    transition width, whose exact definition the text does not print)."""
+    from scipy.optimize import minimize
+    r = np.asarray(rhos, np.float64)
+    kk = np.asarray(recovered, np.float64)
+    nn = np.broadcast_to(np.asarray(problems, np.float64), r.shape)
+
+    def nll(th):
+        z = (r - th[0]) / math.exp(th[1])
+        # log P = -log(1 + e^z), log(1 - P) = z - log(1 + e^z)
+        lse = np.logaddexp(0.0, z)
+        return float(np.sum(kk * lse + (nn - kk) * (lse - z)))
+
+    frac = kk / nn
+    above = r[frac >= 0.5]
+    r0 = float(above.max()) if above.size else float(r.min())
+    best = None
+    for w0 in (0.003, 0.01, 0.03):
+        res = minimize(nll, np.array([r0, math.log(w0)]), method="L-BFGS-B",
+                       bounds=[(float(r.min()) - 0.5, float(r.max()) + 0.5), (math.log(1e-4), math.log(1.0))])
+        if best is None or res.fun < best.fun:
+            best = res
+    rho50, w = float(best.x[0]), math.exp(float(best.x[1]))
+    return rho50, w, 2.0 * math.log(9.0) * w
 
 
 def cell(delta, sigma, n, d=7, problems=10, rho_step=0.01, rho_max=0.5, adaptive=False, quantised=False,
@@ -87,9 +119,10 @@ def main(argv=None):
     a = ap.parse_args(argv)
     rows, rho_star = cell(a.delta, a.sigma, 1 << a.log2n, a.d, a.problems, a.rho_step, a.rho_max, a.adaptive,
                           a.quantised, a.seed, out=sys.stdout)
+    rho50, w, width = fit_logistic([r["rho"] for r in rows], [r["recovered"] for r in rows], a.problems)
     print(json.dumps({"summary": True, "delta": a.delta, "sigma": a.sigma, "n": 1 << a.log2n,
-                      "adaptive_k": int(a.adaptive), "quantised": int(a.quantised), "rho_star": rho_star}),
-          flush=True)
+                      "adaptive_k": int(a.adaptive), "quantised": int(a.quantised), "rho_star": rho_star,
+                      "rho50_logistic": rho50, "width_90_10": width}), flush=True)
 
 
 if __name__ == "__main__":
