@@ -350,26 +350,39 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a)
 template <int NT>
 __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
 {
+    // The state is read once into shared memory (warp 0, one word per lane,
+    // through L2: other CTAs of this launch wrote to it), decided on there,
+    // and written back once, so thread 0's decisions wait on no global loads.
+    constexpr int SW = sizeof(DecodeState) / 4;
+    static_assert(sizeof(DecodeState) % 4 == 0 && SW <= 32, "one word per lane of warp 0");
+    __shared__ DecodeState S;
     __shared__ double s_l1;
     __shared__ int s_acc;
     DecodeState *st = a.st;
     const int t = threadIdx.x;
     const DecodeCtx *ctx = a.ctx;
     float *x = ctx->x;
-    if (t == 0) s_acc = 0;
-    if (upd > 0) {
-        if (t < 32) {
+    if (t < 32) {
+        if (t < SW) ((unsigned *)&S)[t] = __ldcg((const unsigned *)st + t);
+        double v = 0.0;
+        if (upd > 0) {
             // ||r||_1 of the candidate: chunk partials combined in a fixed order
-            double v = 0.0;
             for (int c = t; c < a.nchunks; c += 32) v += __ldcg(a.l1part + c);
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (t == 0) { s_l1 = v; s_acc = ctx->always_accept ? 1 : (v < st->l1_hat); }
         }
-        __syncthreads();
+        __syncwarp();
+        if (t == 0) {
+            S.rb_done = 0u;                        // the rebuild's last-CTA count starts over
+            s_l1 = v;
+            s_acc = (upd > 0) ? (ctx->always_accept ? 1 : (v < S.l1_hat)) : 0;
+        }
+    }
+    __syncthreads();
+    if (upd > 0) {
         if (s_acc) {
-            if (st->drop_count > 0 || st->zeroed > 0) {
+            if (S.drop_count > 0 || S.zeroed > 0) {
                 // entries became zero: stable in-place compaction of the list
-                const unsigned total = st->list_count;
+                const unsigned total = S.list_count;
                 unsigned out = 0;
                 for (unsigned base = 0; base < total; base += NT) {
                     const unsigned e = base + t;
@@ -391,61 +404,63 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
                     out += blk;
                     __syncthreads();
                 }
-                if (t == 0) st->list_count = out;
+                if (t == 0) S.list_count = out;
             }
             if (t == 0) {
-                st->shat_count = st->list_count;
-                st->nnz = (unsigned)((int)st->nnz + st->nnz_delta - (int)st->drop_count);
-                st->cur ^= 1;
-                st->l1_hat = s_l1;
-                st->accepted_rounds += 1;
+                S.shat_count = S.list_count;
+                S.nnz = (unsigned)((int)S.nnz + S.nnz_delta - (int)S.drop_count);
+                S.cur ^= 1;
+                S.l1_hat = s_l1;
+                S.accepted_rounds += 1;
             }
         } else {
-            const unsigned nd = st->drop_count;
+            const unsigned nd = S.drop_count;
             for (unsigned e = t; e < nd; e += NT) x[a.dlog[e].j] = a.dlog[e].old;
             __syncthreads();
             for (unsigned e = t; e < upd; e += NT) x[a.ulog[e].j] = a.ulog[e].old;
-            if (t == 0) st->list_count = st->shat_count;
+            if (t == 0) S.list_count = S.shat_count;
         }
         __syncthreads();
     }
     if (t == 0) {
-        const int round = st->round;
-        const double l1n = (upd > 0) ? s_l1 : st->l1_hat;
+        const int round = S.round;
+        const double l1n = (upd > 0) ? s_l1 : S.l1_hat;
         if (ctx->want_log && round < RL0_MAX_ROUNDS) {
             RoundLog L;
             L.l1_candidate = l1n;
-            L.l1_hat = st->l1_hat;
+            L.l1_hat = S.l1_hat;
             L.accepted = s_acc;
             L.updated = (int)upd;
-            L.support = (int)st->nnz;
-            L.hk_dropped = (int)st->drop_count;
+            L.support = (int)S.nnz;
+            L.hk_dropped = (int)S.drop_count;
             a.rlog[round] = L;
         }
-        if (upd > 0 && st->drop_count > 0) st->hk_rounds += 1;
-        if (upd > 0 && st->overflow) st->fallback_rounds += 1;
-        st->upd_count = 0;
-        st->drop_count = 0;
-        st->overflow = 0;
-        st->nnz_delta = 0;
-        st->zeroed = 0;
-        st->round = round + 1;
-        st->rounds_run += 1;
-        st->iters += 1;
-        st->l1_new = l1n;
+        if (upd > 0 && S.drop_count > 0) S.hk_rounds += 1;
+        if (upd > 0 && S.overflow) S.fallback_rounds += 1;
+        S.upd_count = 0;
+        S.drop_count = 0;
+        S.overflow = 0;
+        S.nnz_delta = 0;
+        S.zeroed = 0;
+        S.round = round + 1;
+        S.rounds_run += 1;
+        S.iters += 1;
+        S.l1_new = l1n;
         if (ctx->always_accept) {
             // Alg. 1: every iteration is kept; it ends when one changes nothing
-            if (upd > 0) st->big_hat = __ldcg(&st->big_cand);
-            st->converged = (st->big_hat == 0);
-            if (upd == 0) st->done = 1;
+            if (upd > 0) S.big_hat = S.big_cand;
+            S.converged = (S.big_hat == 0);
+            if (upd == 0) S.done = 1;
         } else {
-            st->converged = (st->l1_hat <= ctx->stop_level);
+            S.converged = (S.l1_hat <= ctx->stop_level);
         }
-        st->big_cand = 0;
-        if (st->converged || st->round >= ctx->nrounds || st->iters > (unsigned)ctx->nrounds || st->status != 0)
-            st->done = 1;
-        if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
+        S.big_cand = 0;
+        if (S.converged || S.round >= ctx->nrounds || S.iters > (unsigned)ctx->nrounds || S.status != 0)
+            S.done = 1;
     }
+    __syncthreads();
+    if (t < SW) ((unsigned *)st)[t] = ((const unsigned *)&S)[t];
+    if (t == 0 && a.has_cond) cudaGraphSetConditional(a.cond, S.done ? 0u : 1u);
 }
 
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
@@ -659,8 +674,22 @@ struct GraphEntry {
     std::vector<cudaEvent_t> events;   // profile: 4 per round + 1, boundaries of the kernel groups
 };
 
-// Kernels one decode graph launches: prologue (3), 3 per round, final check (1).
-int launches_per_decode(int nrounds) { return 3 + 3 * nrounds + 1; }
+// Rounds per iteration of the graph's WHILE loop: one iteration of the
+// conditional node costs about as much as a kernel launch, so two rounds share
+// one; after an odd number of rounds the second round's kernels only see the
+// done flag and exit.
+#define RL0_ROUNDS_PER_ITER 2
+
+// Kernels one decode graph launches: prologue (3), 3 per round in whole loop
+// iterations, final check (1).
+int launches_per_decode(int nrounds)
+{
+    const int iters = (nrounds + RL0_ROUNDS_PER_ITER - 1) / RL0_ROUNDS_PER_ITER;
+    return 3 + 3 * RL0_ROUNDS_PER_ITER * iters + 1;
+}
+
+// The same with every round launched on its own (profile graph, direct launches).
+int launches_unrolled(int nrounds) { return 3 + 3 * nrounds + 1; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -729,11 +758,11 @@ void launch_round(const KArgs &a, int dmax, int indicator, int learned, cudaStre
 }
 
 // The round loop as a graph.  Normal decodes: prologue kernels, then a WHILE
-// conditional node whose body is one round (the accept kernel clears the
-// condition once the decode is done, so no kernel runs after convergence),
-// then the FP64 residual check.  Profile decodes: the rounds unrolled, with
-// event-record nodes around each kernel group (event nodes are not allowed in
-// a conditional body).
+// conditional node whose body is RL0_ROUNDS_PER_ITER rounds (the rebuild's
+// last CTA clears the condition once the decode is done; a round after that
+// only sees the done flag), then the FP64 residual check.  Profile decodes:
+// the rounds unrolled, with event-record nodes around each kernel group (event
+// nodes are not allowed in a conditional body).
 int add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep, void *func,
                     unsigned grid, unsigned block, KArgs *a, void **extra, int nextra)
 {
@@ -791,7 +820,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
                 cudaSuccess) { rc = RL0_ERR_CUDA; break; }
-            launch_round(a, dmax, indicator, learned, s);
+            for (int q = 0; q < RL0_ROUNDS_PER_ITER; ++q) launch_round(a, dmax, indicator, learned, s);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
             if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_sum, 1, 32, &a, nullptr, 0))) break;
@@ -1155,7 +1184,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         stats->ms = ms;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = launches_per_decode(prof ? R.nrounds : H->st.rounds_run);
+        stats->launches = prof ? launches_unrolled(R.nrounds) : launches_per_decode(H->st.rounds_run);
         if (prof) {
             float acc[4] = {0, 0, 0, 0};
             const int active = H->st.rounds_run < R.nrounds ? H->st.rounds_run : R.nrounds;
@@ -1556,7 +1585,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
         stats->final_l1 = l1;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = launches_per_decode(R.nrounds);
+        stats->launches = launches_unrolled(R.nrounds);
     }
     return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
 }

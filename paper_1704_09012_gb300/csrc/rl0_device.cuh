@@ -43,17 +43,30 @@ __device__ __forceinline__ float series_eval(const Series &S, float w)
 }
 
 // Fixed-shape FP64 tree over `n` consecutive threads starting at `base`
-// (n a power of two): sh[t] += sh[t + off] for off = n/2 .. 1.  Every thread
-// of the block must call it (it synchronises the block).
+// (n a power of two, 64 <= n): sh[t] += sh[t + off] for off = n/2 .. 1.  The
+// levels off >= 32 go through shared memory, the last five through warp
+// shuffles in the group's first warp: the same additions in the same order.
+// Every thread of the block must call it (it synchronises the block).
 __device__ __forceinline__ double group_sum_f64(double v, double *sh, int lane, int n)
 {
     sh[lane] = v;
     __syncthreads();
-    for (int off = n >> 1; off > 0; off >>= 1) {
+    for (int off = n >> 1; off >= 32; off >>= 1) {
         if (lane < off) sh[lane] += sh[lane + off];
         __syncthreads();
     }
-    const double r = sh[0];
+    double r = 0.0;
+    if (lane < 32) {
+        r = sh[lane];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double u = __shfl_down_sync(0xffffffffu, r, off);
+            if (lane < off) r += u;
+        }
+        if (lane == 0) sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
     __syncthreads();
     return r;
 }
@@ -63,13 +76,13 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
     return group_sum_f64(v, sh, threadIdx.x, blockDim.x);
 }
 
-// Two block_sum_f64 trees in one pass (the same adds in the same order).
+// Two block_sum_f64 trees in one pass (the same additions in the same order).
 __device__ __forceinline__ double2 block_sum2_f64(double a, double b, double2 *sh)
 {
     const int t = threadIdx.x, n = blockDim.x;
     sh[t] = make_double2(a, b);
     __syncthreads();
-    for (int off = n >> 1; off > 0; off >>= 1) {
+    for (int off = n >> 1; off >= 32; off >>= 1) {
         if (t < off) {
             const double2 u = sh[t + off];
             sh[t].x += u.x;
@@ -77,7 +90,22 @@ __device__ __forceinline__ double2 block_sum2_f64(double a, double b, double2 *s
         }
         __syncthreads();
     }
-    const double2 r = sh[0];
+    double2 r = make_double2(0.0, 0.0);
+    if (t < 32) {
+        r = sh[t];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ux = __shfl_down_sync(0xffffffffu, r.x, off);
+            const double uy = __shfl_down_sync(0xffffffffu, r.y, off);
+            if (t < off) {
+                r.x += ux;
+                r.y += uy;
+            }
+        }
+        if (t == 0) sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
     __syncthreads();
     return r;
 }
