@@ -14,8 +14,9 @@
 //            CTA's slice [lo, hi) of a list in global memory;
 //   resolve  with the codes no longer needed, their shared memory stages the
 //            survivors, NT at a time: one thread per column reads its FP32
-//            (r, p_z) and applies anchor_candidates, one thread per candidate
-//            (column, slot) scores it, and each column takes its highest
+//            (r, p_z) and applies anchor_candidates; the candidates' posteriors
+//            q_e(r_s - r_l) are evaluated one per thread, then one thread per
+//            candidate (column, slot) sums them, and each column takes its highest
 //            passing slot (the last passing anchor in row order); the CTA
 //            then commits with one global atomic per counter;
 //   H_k      the launch's last CTA applies H_k, its scratch in the bytes that
@@ -74,6 +75,7 @@ struct ResScratch {
     unsigned char it_s[NT * DMAX];       // item -> slot (descending within a column)
     unsigned char it_ok[NT * DMAX];
     float it_w[NT * DMAX];
+    float q[NT][DMAX];                   // q_e of (item, slot l), NT items at a time
     unsigned wsum[NT / 32];
 };
 
@@ -260,16 +262,36 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
             }
         }
         __syncthreads();
-        for (unsigned k = tid; k < nitems; k += NT) {
-            const int ee = R.it_e[k], sl = R.it_s[k];
-            float re[DMAX];
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s) re[s] = R.r[s][ee];
-            const AnchorEval E = eval_anchor_regs<DMAX, IND>(re, d, sl, th.te, S.pe);
-            R.it_ok[k] = (E.lhs <= R.rhs[ee] && E.ne - R.nz[ee] >= alpha) ? 1 : 0;
-            R.it_w[k] = E.w;
+        // eval_anchor's arithmetic in two steps, so that an item's d posteriors
+        // are evaluated side by side (one per thread) rather than one after
+        // another: q_e of every (item, l), then each item's sums in slot order
+        for (unsigned k0 = 0; k0 < nitems; k0 += NT) {
+            const unsigned kn = min(nitems - k0, (unsigned)NT);
+            for (unsigned p = tid; p < kn * (unsigned)d; p += NT) {
+                const unsigned kk = p / (unsigned)d, l = p % (unsigned)d;
+                const int ee = R.it_e[k0 + kk], sl = R.it_s[k0 + kk];
+                const float rs = R.r[sl][ee], rl = R.r[l][ee];
+                R.q[kk][l] = IND ? (fabsf(rs - rl) <= th.te ? 1.0f : 0.0f) : series_eval(S.pe, rs - rl);
+            }
+            __syncthreads();
+            for (unsigned kk = tid; kk < kn; kk += NT) {
+                const unsigned k = k0 + kk;
+                const int ee = R.it_e[k];
+                float ne = 0.0f, num = 0.0f;
+                for (int l = 0; l < d; ++l) {
+                    const float rl = R.r[l][ee];
+                    const float q = R.q[kk][l];
+                    ne += q;
+                    num += rl * q;
+                }
+                const float w = num / ne;
+                float lhs = 0.0f;
+                for (int l = 0; l < d; ++l) lhs += fabsf(R.r[l][ee] - w);
+                R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= alpha) ? 1 : 0;
+                R.it_w[k] = w;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         // each column: its first passing item is its highest passing slot
         int best = -1;
         float bw = 0.0f;
