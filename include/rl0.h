@@ -70,7 +70,7 @@ typedef struct {
 
 /* Per-decode statistics (host structure filled by the library). */
 typedef struct {
-    int     rounds;            /* rounds executed (including t = 1)                          */
+    int     rounds;            /* rounds of the sweep, including t = 1 (see skipped_rounds)  */
     int     accepted_rounds;   /* rounds whose candidate passed ||r||_1 < ||r_hat||_1        */
     int     converged;         /* 1 if ||r_hat||_1 <= m sigma_n sqrt(2/pi) at exit           */
     int     status;            /* RL0_OK, or the device-side error of this decode            */
@@ -81,13 +81,17 @@ typedef struct {
     int     fallback_rounds;   /* rounds whose residual took the full CSR rebuild            */
     /* profile = 1 only: summed device time of each kernel group over the rounds the decode
      * ran (event nodes around the groups, so each interval includes the launch gap) */
-    float   ms_score;          /* column scoring                                             */
-    float   ms_hk;             /* H_k selection                                              */
-    float   ms_rebuild;        /* scatter + residual rebuild                                 */
-    float   ms_accept;         /* accept / undo                                              */
+    float   ms_score;          /* column scoring, with H_k in the kernel's last CTA          */
+    float   ms_hk;             /* from the scoring kernel's end to the scatter's start       */
+    float   ms_rebuild;        /* scatter + residual rebuild, with accept/undo in the        */
+                               /* rebuild's last CTA                                         */
+    float   ms_accept;         /* from the rebuild's end to the next round's start           */
     int     launches;          /* kernels launched by the decode (any mode)                  */
     int     analytic_rounds;   /* scorer = 1: rounds of the analytic continuation (0 if the  */
                                /* learned decode converged on its own)                       */
+    int     skipped_rounds;    /* rounds counted in `rounds` that launched no kernels: with   */
+                               /* sigma_n > 0 the round at t = 1 provably changes nothing    */
+                               /* (its anchor test needs p_z = 0) and is only recorded       */
 } rl0_stats;
 
 /* Def. "Generating model", item 1: draw A with each column's support uniform

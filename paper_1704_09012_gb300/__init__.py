@@ -60,7 +60,7 @@ class Stats(C.Structure):
         ("support_size", C.c_int64), ("final_l1", C.c_double), ("ms", C.c_float), ("hk_rounds", C.c_int),
         ("fallback_rounds", C.c_int), ("ms_score", C.c_float), ("ms_hk", C.c_float),
         ("ms_rebuild", C.c_float), ("ms_accept", C.c_float), ("launches", C.c_int),
-        ("analytic_rounds", C.c_int),
+        ("analytic_rounds", C.c_int), ("skipped_rounds", C.c_int),
     ]
 
     def as_dict(self):

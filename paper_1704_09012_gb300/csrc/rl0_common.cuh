@@ -81,6 +81,7 @@ struct DecodeState {
     unsigned rb_done;         // CTAs of the rebuild finished (last one accepts or undoes)
     unsigned big_hat;         // Alg. 1 mode: rows of r_hat with |r_i| > conv_tol
     unsigned big_cand;        // Alg. 1 mode: the same count for the candidate r
+    int skipped;              // rounds recorded without running their kernels (the t = 1 round)
     int rounds_run;
     int accepted_rounds;
     int hk_rounds;
@@ -116,6 +117,7 @@ struct DecodeCtx {
     int want_log;
     int no_accept;            // round_step: stop after the rebuild (no accept, no undo)
     int always_accept;        // Alg. 1 (Parallel-l0): keep every iteration, stop when one changes nothing
+    int skip_t1;              // sigma_n > 0: the round at t = 1 provably changes nothing; record it only
     float conv_tol;           // Alg. 1: converged when every |r_i| <= conv_tol (0: Alg. 2's stop level)
 };
 

@@ -106,6 +106,26 @@ __global__ void k_start(KArgs a, int round0, int empty_support)
     st->nnz_delta = 0;
     st->zeroed = 0;
     st->iters = 0;
+    st->skipped = 0;
+    if (!st->done && round0 == 0 && a.ctx->skip_t1) {
+        // the round at t = 1 changes nothing (sigma_n > 0): record it as the
+        // accept step records an empty round, and start at the next one
+        if (a.ctx->want_log) {
+            RoundLog L;
+            L.l1_candidate = l1;
+            L.l1_hat = l1;
+            L.accepted = 0;
+            L.updated = 0;
+            L.support = (int)st->nnz;
+            L.hk_dropped = 0;
+            a.rlog[0] = L;
+        }
+        st->round = 1;
+        st->rounds_run = 1;
+        st->iters = 1;
+        st->skipped = 1;
+        st->done = (1 >= a.ctx->nrounds);
+    }
     if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
 }
 
@@ -1059,7 +1079,8 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
     std::vector<std::pair<int, float>> supp;
     std::vector<float> vals;
     int launches = 3;
-    for (int r = 0; r < R.nrounds && !H->st.done; ++r) {
+    for (int r = 0; r < H->st.round && r < RL0_MAX_ROUNDS; ++r) H->kprior[r] = kprior;   // recorded rounds
+    for (int r = H->st.round; r < R.nrounds && !H->st.done; ++r) {
         H->kprior[r] = kprior;
         launch_round(a, dmax, R.indicator, 0, s);
         launches += 3;
@@ -1129,6 +1150,7 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
         stats->launches = launches;
+        stats->skipped_rounds = H->st.skipped;
     }
     if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
     return RL0_OK;
@@ -1184,10 +1206,12 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         stats->ms = ms;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = prof ? launches_unrolled(R.nrounds) : launches_per_decode(H->st.rounds_run);
+        stats->launches = prof ? launches_unrolled(R.nrounds) : launches_per_decode(H->st.rounds_run - H->st.skipped);
+        stats->skipped_rounds = H->st.skipped;
         if (prof) {
             float acc[4] = {0, 0, 0, 0};
-            const int active = H->st.rounds_run < R.nrounds ? H->st.rounds_run : R.nrounds;
+            const int ran = H->st.rounds_run - H->st.skipped;   // launch groups that did a round
+            const int active = ran < R.nrounds ? ran : R.nrounds;
             for (int r = 0; r < active; ++r)            // rounds after the decode finished only exit
                 for (int q = 0; q < 4; ++q) {
                     float v = 0.0f;
@@ -1244,6 +1268,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
             stats->hk_rounds = first.hk_rounds + H->st.hk_rounds;
             stats->fallback_rounds = first.fallback_rounds + H->st.fallback_rounds;
             stats->analytic_rounds = H->st.rounds_run;
+            stats->skipped_rounds = first.skipped + H->st.skipped;
             stats->launches += 4 + 3 * R2.nrounds + 1;
         }
     }
@@ -1405,6 +1430,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     H->ctx.want_log = 0;
     H->ctx.passed = passed_dev;
     H->ctx.no_accept = 1;
+    H->ctx.skip_t1 = 0;                            // run exactly the round asked for
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
@@ -1586,6 +1612,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
         stats->launches = launches_unrolled(R.nrounds);
+        stats->skipped_rounds = H->st.skipped;
     }
     return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
 }

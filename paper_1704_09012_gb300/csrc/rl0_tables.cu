@@ -271,6 +271,9 @@ void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx,
     ctx->logit_thr = (float)std::log(th / (1.0 - th));
     ctx->learned_need = 1.5f;
     ctx->inv_sn = (p.sigma_n > 0.0) ? (float)(1.0 / p.sigma_n) : 0.0f;
+    // reading: at t = 1 the anchor test 1 - p_z(r) >= 1 needs p_z(r) = 0, which
+    // never holds for sigma_n > 0, so the first round updates nothing
+    ctx->skip_t1 = (p.sigma_n > 0.0) ? 1 : 0;
     ctx->drho = (float)(d * rho);
     HostSeries hz, he;
     if (p.sigma_n > 0.0) {
