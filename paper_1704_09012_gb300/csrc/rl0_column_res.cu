@@ -10,15 +10,19 @@
 //            row ids from HBM (one coalesced 4-byte load per slot; the next
 //            tile's are prefetched) and its d codes from shared memory, and
 //            bounds the column's anchors with code_candidates; no thread
-//            waits on another, and the few columns that survive go on the
-//            CTA's slice [lo, hi) of a list in global memory;
+//            waits on another; a column that survives (about 1%) is listed
+//            with its candidate slots: the first res_qcap of a CTA in shared
+//            memory, where asynchronous copies (cp.async) fetch its FP32
+//            (r, p_z) and x_j while the stream goes on, the rest in the CTA's
+//            slice [lo, hi) of a list in global memory;
 //   resolve  with the codes no longer needed, their shared memory stages the
-//            survivors, NT at a time: one thread per column reads its FP32
-//            (r, p_z) and applies anchor_candidates; the candidates' posteriors
-//            q_e(r_s - r_l) are evaluated one per thread, then one thread per
-//            candidate (column, slot) sums them, and each column takes its highest
-//            passing slot (the last passing anchor in row order); the CTA
-//            then commits with one global atomic per counter;
+//            survivors, NT at a time: one thread per column takes its FP32
+//            (r, p_z) and keeps the candidate slots that are anchors
+//            (|r_s| >= t_a); the candidates' posteriors q_e(r_s - r_l) are
+//            evaluated one per thread, then one thread per candidate (column,
+//            slot) sums them, and each column takes its highest passing slot
+//            (the last passing anchor in row order); the CTA then commits with
+//            one global atomic per counter;
 //   H_k      the launch's last CTA applies H_k, its scratch in the bytes that
 //            held the codes.
 // The resolve runs the arithmetic of k_column_score in the same order, so
@@ -41,6 +45,29 @@ struct ResShared {
     int count, last;
     unsigned total, ubase, fbase;
 };
+
+// A survivor staged in shared memory: its column, candidate slots, x_j and
+// the (r, p_z) of its rows, the last two copied with cp.async.
+template <int DMAX>
+struct ResEntry {
+    int j;
+    unsigned mask;
+    float old, pad;
+    float2 rz[DMAX];
+};
+static_assert(sizeof(ResEntry<7>) == 16 + 8 * 7 && sizeof(ResEntry<32>) == 16 + 8 * 32, "entry layout");
+
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
 
 // Bytes of the code region, which later holds the resolve scratch and, in
 // the last CTA, H_k's scratch.
@@ -175,12 +202,15 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         j0 = hi;
     }
     const CodeThr ct = code_thresholds(th.ta, th.tz, IND ? th.te : S.pe.cut);
-    const float b1 = ctx->pe_b1, c1 = ctx->pe_c1;
     const float need = IND ? ctx->alpha : ctx->alpha - 1e-3f;
     int32_t *passed = ctx->passed;
     const int lane = tid & 31;
-    // this CTA's slice of the survivor list: entries (j, its d row ids)
-    int *seg = a.res_list + (size_t)lo * (size_t)(DMAX + 1);
+    // this CTA's survivors: the first qcap in shared memory, the others in its
+    // slice of the global list, entries (j, candidate mask, its d row ids)
+    ResEntry<DMAX> *sq = (ResEntry<DMAX> *)(dsm + a.res_q_off);
+    const int qcap = a.res_qcap;
+    int *seg = a.res_list + (size_t)lo * (size_t)(DMAX + 2);
+    const float *xg = ctx->x;
     for (; j0 < hi; j0 += NT) {
         int rid[DMAX];
 #pragma unroll
@@ -193,8 +223,8 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         }
         const int j = j0 + tid;
         const bool active = j < hi;
-        const bool cand =
-            active && code_candidates<DMAX, IND>(s_code, s_pz, rid, d, ct, need) != 0u;
+        const unsigned cm = active ? code_candidates<DMAX, IND>(s_code, s_pz, rid, d, ct, need) : 0u;
+        const bool cand = cm != 0u;
         const unsigned m = __ballot_sync(0xffffffffu, cand);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -202,50 +232,69 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
             if (lane == leader) base = atomicAdd(&S.count, __popc(m));
             base = __shfl_sync(0xffffffffu, base, leader);
             const int pos = base + __popc(m & ((1u << lane) - 1u));
-            if (cand && pos < hi - lo) {            // pos < hi - lo always: one entry per column
-                int *ent = seg + (size_t)pos * (DMAX + 1);
-                ent[0] = j;
+            if (cand && pos < qcap) {
+                ResEntry<DMAX> &q = sq[pos];
+                q.j = j;
+                q.mask = cm;
+                cp_async_4(&q.old, xg + j);
 #pragma unroll
                 for (int s = 0; s < DMAX; ++s)
-                    if (s < d) ent[1 + s] = rid[s];
+                    if (s < d) cp_async_8(&q.rz[s], rz + rid[s]);
+            } else if (cand && pos < hi - lo) {     // pos < hi - lo always: one entry per column
+                int *ent = seg + (size_t)pos * (DMAX + 2);
+                ent[0] = j;
+                ent[1] = (int)cm;
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s)
+                    if (s < d) ent[2 + s] = rid[s];
             }
         }
         if (passed && active && !cand) passed[j] = 0;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();                               // the stream is done: the codes' bytes become scratch
     const int count = min(S.count, hi - lo);
     ResScratch<DMAX, NT> &R = *(ResScratch<DMAX, NT> *)dsm;
     const float alpha = ctx->alpha;
-    const float reach = IND ? th.te : S.pe.cut;
     for (int b0 = 0; b0 < count; b0 += NT) {
         // one thread per listed column: FP32 residuals, exact candidates
         const int e = b0 + tid;
         const bool act = e < count;
-        const int *ent = seg + (size_t)(act ? e : 0) * (DMAX + 1);
-        const int j = act ? __ldcg(ent) : 0;
+        int j = 0;
         unsigned cand = 0u;
         float old = 0.0f;
         if (act) {
-            int rid[DMAX];
+            float2 v[DMAX];
+            unsigned cm;
+            if (e < qcap) {
+                const ResEntry<DMAX> &q = sq[e];
+                j = q.j;
+                cm = q.mask;
+                old = q.old;
 #pragma unroll
-            for (int s = 0; s < DMAX; ++s) rid[s] = (s < d) ? __ldcg(ent + 1 + s) : 0;
-            old = ctx->x[j];
-            float r[DMAX];
+                for (int s = 0; s < DMAX; ++s) v[s] = (s < d) ? q.rz[s] : make_float2(0.0f, 0.0f);
+            } else {
+                const int *ent = seg + (size_t)e * (DMAX + 2);
+                j = __ldcg(ent);
+                cm = (unsigned)__ldcg(ent + 1);
+                old = xg[j];
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s) v[s] = (s < d) ? __ldg(rz + __ldcg(ent + 2 + s)) : make_float2(0.0f, 0.0f);
+            }
             float nz = 0.0f, rhs = 0.0f;
 #pragma unroll
             for (int s = 0; s < DMAX; ++s) {
-                r[s] = 0.0f;
                 if (s < d) {
-                    const float2 v = __ldg(rz + rid[s]);
-                    r[s] = v.x;
-                    nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
-                    rhs += fabsf(v.x);
+                    nz += IND ? (fabsf(v[s].x) <= th.tz ? 1.0f : 0.0f) : v[s].y;
+                    rhs += fabsf(v[s].x);
+                    // the code bound's candidates that are anchors: a superset of
+                    // the passing anchors, each then tested exactly below
+                    if (((cm >> s) & 1u) && fabsf(v[s].x) >= th.ta) cand |= 1u << s;
                 }
-                R.r[s][tid] = r[s];
+                R.r[s][tid] = (s < d) ? v[s].x : 0.0f;
             }
             R.nz[tid] = nz;
             R.rhs[tid] = rhs;
-            cand = anchor_candidates<DMAX, IND>(r, d, th.ta, reach, b1, c1, nz, need);
         }
         // one item per candidate (column, slot), a column's slots in descending order
         const unsigned nc = (unsigned)__popc(cand);
@@ -312,11 +361,11 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         const bool fresh = pass && old == 0.0f && nv != 0.0f;
         const unsigned pf = cta_exclusive_scan<NT>((pass ? 0x10000u : 0u) | (fresh ? 1u : 0u), R.wsum, &S.total);
         const unsigned tpf = S.total;
+        // entries that became zero; the fresh ones are the scan's low field
         const int ngone = __syncthreads_count(pass && old != 0.0f && nv == 0.0f);
-        const int nup = __syncthreads_count(pass && old == 0.0f && nv != 0.0f);
-        const int ndown = __syncthreads_count(pass && old != 0.0f && nv == 0.0f);
         if (tid == 0) {
-            if (nup != ndown) atomicAdd(&st->nnz_delta, nup - ndown);
+            const int nup = (int)(tpf & 0xffffu);
+            if (nup != ngone) atomicAdd(&st->nnz_delta, nup - ngone);
             if (ngone) atomicAdd(&st->zeroed, (unsigned)ngone);
             S.ubase = (tpf >> 16) ? atomicAdd(&st->upd_count, tpf >> 16) : 0u;
             S.fbase = (tpf & 0xffffu) ? atomicAdd(&st->list_count, tpf & 0xffffu) : 0u;
@@ -392,13 +441,18 @@ void rl0_res_setup(const rl0_expander *A, KArgs *a)
     const unsigned region = res_region_bytes(A->m, nt, res_scratch_bytes(A->d));
     a->res_pz_off = region;
     a->res_s_off = region + 4u * RL0_PZ_BINS;
-    a->res_smem = a->res_s_off + (unsigned)sizeof(ResShared);
+    a->res_q_off = (a->res_s_off + (unsigned)sizeof(ResShared) + 15u) & ~15u;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, A->device) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
-    if (a->res_smem > (unsigned)optin) return;
+    if (a->res_q_off > (unsigned)optin) return;
+    // the shared memory left over stages survivors (one CTA per SM: nothing
+    // else competes for it); the others go to the global list
+    const unsigned eb = 16u + 8u * (unsigned)res_variant(A->d);
+    a->res_qcap = (int)std::min<unsigned>(((unsigned)optin - a->res_q_off) / eb, 4096u);
+    a->res_smem = a->res_q_off + (unsigned)a->res_qcap * eb;
     bool ok = false;
     switch (res_variant(A->d)) {
     case 6: ok = res_attr<6, true>(a->res_smem); break;

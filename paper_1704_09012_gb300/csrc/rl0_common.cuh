@@ -131,7 +131,7 @@ struct Workspace {
     float2 *rz[2];            // (r_i, p_z(r_i)) for r_hat and the candidate r
     unsigned short *code[2];  // 16-bit codes of the same residuals, padded to a multiple of 8 rows
     float *pzlb;              // p_z lower bound per code bin, float[RL0_PZ_BINS]
-    int *res_list;            // survivors of the column kernel's code bound, n entries (rl0_res_dmax)
+    int *res_list;            // survivors of the column kernel's code bound, n entries of rl0_res_dmax + 2 ints
     int *list;                // support + new nonzeros, capacity n
     int *list_tmp;            // compaction scratch, capacity n
     UndoEntry *ulog;          // updates of this round, capacity n

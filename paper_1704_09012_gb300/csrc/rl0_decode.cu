@@ -919,7 +919,7 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.code[0], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
     al((void **)&w.code[1], (size_t)rl0_code_rows(A->m) * sizeof(unsigned short));
     al((void **)&w.pzlb, RL0_PZ_BINS * sizeof(float));
-    al((void **)&w.res_list, n * (size_t)(rl0_res_dmax(A->d) + 1) * sizeof(int));
+    al((void **)&w.res_list, n * (size_t)(rl0_res_dmax(A->d) + 2) * sizeof(int));
     al((void **)&w.list, n * sizeof(int));
     al((void **)&w.list_tmp, sizeof(int));
     al((void **)&w.ulog, n * sizeof(UndoEntry));

@@ -16,8 +16,10 @@ struct KArgs {
     const float *pzlb;                 // p_z lower bound per code bin
     int res_ok;                        // the column kernel holds every row's code in shared memory
     int res_grid;                      // its CTAs (one per SM)
-    unsigned res_pz_off, res_s_off, res_smem;   // its dynamic shared-memory layout
-    int *res_list;                     // its survivors: n entries of (j, DMAX row ids); CTA b uses its column range
+    unsigned res_pz_off, res_s_off, res_q_off, res_smem;   // its dynamic shared-memory layout
+    int res_qcap;                      // survivors per CTA staged in shared memory (FP32 residuals and x_j)
+    int *res_list;                     // its other survivors: n entries of (j, candidate mask, DMAX row ids);
+                                       // CTA b uses its column range
     int *list;
     UndoEntry *ulog, *dlog;
     int *bcnt, *bkt;
