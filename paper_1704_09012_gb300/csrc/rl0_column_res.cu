@@ -141,6 +141,8 @@ __device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsu
 template <int DMAX, bool IND, bool EXACT, int NT>
 __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
 {
+    // exact d <= 8: two columns per thread in FP16 lanes (code_candidates2)
+    constexpr bool PAIRED = EXACT && DMAX <= 8;
     extern __shared__ __align__(16) unsigned char dsm[];
     DecodeState *st = a.st;
     if (st->done) return;
@@ -184,11 +186,14 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
     const int lo = (int)(((long long)blockIdx.x * n) / gridDim.x);
     const int hi = (int)(((long long)(blockIdx.x + 1) * n) / gridDim.x);
     int j0 = lo;
-    int nxt[DMAX];
+    // row ids of this thread's first column(s): j0 + tid (and j0 + NT + tid
+    // when paired)
+    int nxt[DMAX], nxb[PAIRED ? DMAX : 1];
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
         const int j = j0 + tid;
         nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+        if constexpr (PAIRED) nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
     }
     __syncthreads();                               // the barrier is initialised
     const bool arrived = mbar_try_wait_bounded(bar, 0u);
@@ -211,6 +216,73 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
     const int qcap = a.res_qcap;
     int *seg = a.res_list + (size_t)lo * (size_t)(DMAX + 2);
     const float *xg = ctx->x;
+    // list column j (candidate mask cm, row ids rid) at position pos
+    auto emit = [&](int j, unsigned cm, int pos, const int *rid) {
+        if (pos < qcap) {
+            ResEntry<DMAX> &q = sq[pos];
+            q.j = j;
+            q.mask = cm;
+            cp_async_4(&q.old, xg + j);
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (s < d) cp_async_8(&q.rz[s], rz + rid[s]);
+        } else if (pos < hi - lo) {                 // pos < hi - lo always: one entry per column
+            int *ent = seg + (size_t)pos * (DMAX + 2);
+            ent[0] = j;
+            ent[1] = (int)cm;
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (s < d) ent[2 + s] = rid[s];
+        }
+    };
+    if constexpr (PAIRED) {
+        // two columns per thread, j and j + NT, bounded side by side in FP16
+        // lanes; a listed column reads its row ids again (from L2)
+        const CodeThr2 ct2 = code_thresholds2(ct, need);
+        for (; j0 < hi; j0 += 2 * NT) {
+            int ra[DMAX], rb[DMAX];
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) {
+                ra[s] = nxt[s];
+                rb[s] = nxb[s];
+            }
+            {
+                const int jn = j0 + 2 * NT + tid;
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s) {
+                    if (jn < hi) nxt[s] = __ldg(a.rows_sm + (size_t)s * n + jn);
+                    if (jn + NT < hi) nxb[s] = __ldg(a.rows_sm + (size_t)s * n + jn + NT);
+                }
+            }
+            const int ja = j0 + tid, jb = ja + NT;
+            const bool aa = ja < hi, ab = jb < hi;
+            unsigned ma, mb;
+            code_candidates2<DMAX, IND>(s_code, s_pz, ra, rb, aa, ab, ct2, ma, mb);
+            const unsigned ba = __ballot_sync(0xffffffffu, ma != 0u), bb = __ballot_sync(0xffffffffu, mb != 0u);
+            if (ba | bb) {
+                const int leader = __ffs(ba | bb) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&S.count, __popc(ba) + __popc(bb));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                const unsigned lt = (1u << lane) - 1u;
+                int rr[DMAX];
+                if (ma) {
+#pragma unroll
+                    for (int s = 0; s < DMAX; ++s) rr[s] = __ldg(a.rows_sm + (size_t)s * n + ja);
+                    emit(ja, ma, base + __popc(ba & lt), rr);
+                }
+                if (mb) {
+#pragma unroll
+                    for (int s = 0; s < DMAX; ++s) rr[s] = __ldg(a.rows_sm + (size_t)s * n + jb);
+                    emit(jb, mb, base + __popc(ba) + __popc(bb & lt), rr);
+                }
+            }
+            if (passed) {
+                if (aa && !ma) passed[ja] = 0;
+                if (ab && !mb) passed[jb] = 0;
+            }
+        }
+    }
     for (; j0 < hi; j0 += NT) {
         int rid[DMAX];
 #pragma unroll
@@ -231,23 +303,7 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
             int base = 0;
             if (lane == leader) base = atomicAdd(&S.count, __popc(m));
             base = __shfl_sync(0xffffffffu, base, leader);
-            const int pos = base + __popc(m & ((1u << lane) - 1u));
-            if (cand && pos < qcap) {
-                ResEntry<DMAX> &q = sq[pos];
-                q.j = j;
-                q.mask = cm;
-                cp_async_4(&q.old, xg + j);
-#pragma unroll
-                for (int s = 0; s < DMAX; ++s)
-                    if (s < d) cp_async_8(&q.rz[s], rz + rid[s]);
-            } else if (cand && pos < hi - lo) {     // pos < hi - lo always: one entry per column
-                int *ent = seg + (size_t)pos * (DMAX + 2);
-                ent[0] = j;
-                ent[1] = (int)cm;
-#pragma unroll
-                for (int s = 0; s < DMAX; ++s)
-                    if (s < d) ent[2 + s] = rid[s];
-            }
+            if (cand) emit(j, cm, base + __popc(m & ((1u << lane) - 1u)), rid);
         }
         if (passed && active && !cand) passed[j] = 0;
     }

@@ -441,6 +441,112 @@ __device__ __forceinline__ unsigned code_candidates(const unsigned short *codes,
     return cand;
 }
 
+// code_candidates for two columns at once, d = D rows each, in the two FP16
+// lanes of half2 registers (lane 0: column a, lane 1: column b).  The codes
+// are FP16 values, so the anchor, n_z and count comparisons against a float
+// threshold T are exact when T is first rounded to FP16 in the direction that
+// keeps the test (|v| >= T iff |v| >= RU(T); |v| <= T iff |v| <= RD(T)); the
+// pair test is the one inexact step: |v_s - v_l| is rounded to FP16 (relative
+// error <= 2^-11, absolute <= 2^-25 below 2^-14) and compared with a reach
+// rounded up with that margin, so a pair that can be near always counts.
+// The near count is exact (each pair adds 0 or 1).  Returns the two columns'
+// candidate masks (0 for an inactive column).
+struct CodeThr2 {
+    __half2 ta, tz;                 // RU(ta_lo), RD(tz_in) in both lanes
+    float c1, c0;                   // reach of a column: RU16(c1 vmax + c0)
+    float need1;                    // need - 1
+};
+
+__device__ __forceinline__ CodeThr2 code_thresholds2(const CodeThr &ct, float need)
+{
+    CodeThr2 c;
+    c.ta = __half2half2(__float2half_ru(ct.ta_lo));
+    c.tz = __half2half2(__float2half_rd(ct.tz_in));
+    // reach1 + 2 e(vmax), e(v) = v EREL + EABS, widened by 2^-10 for the FP16
+    // difference and by 2^-20 for this FP32 arithmetic
+    c.c1 = 2.0f * RL0_CODE_EREL * 1.0009775161743164f;
+    c.c0 = fmaf(ct.reach1 + 2.0f * RL0_CODE_EABS, 1.0009775161743164f, 5.9604644775390625e-8f) * RL0_CODE_WIDEN;
+    c.need1 = need - 1.0f;
+    return c;
+}
+
+__device__ __forceinline__ unsigned h2bits(__half2 h) { return *reinterpret_cast<const unsigned *>(&h); }
+
+template <int D, bool IND>
+__device__ __forceinline__ void code_candidates2(const unsigned short *codes, const float *pzlb, const int *ra,
+                                                 const int *rb, bool act_a, bool act_b, const CodeThr2 &ct,
+                                                 unsigned &ma, unsigned &mb)
+{
+    __half2 v[D];
+    __half2 vmax = __float2half2_rn(0.0f), nzi = __float2half2_rn(0.0f);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const unsigned ca = codes[ra[s]], cb = codes[rb[s]];
+        v[s] = __halves2half2(__ushort_as_half((unsigned short)ca), __ushort_as_half((unsigned short)cb));
+        const __half2 av = __habs2(v[s]);
+        vmax = __hmax2(vmax, av);
+        if (IND) nzi = __hadd2(nzi, __hle2(av, ct.tz));
+    }
+    ma = mb = 0u;
+    const float va = __low2float(vmax), vb = __high2float(vmax);
+    const float ta = __low2float(ct.ta);
+    const bool any_a = act_a && va >= ta, any_b = act_b && vb >= ta;
+    if (!(any_a || any_b)) return;
+    const __half2 thr = __halves2half2(__float2half_ru(fmaf(va, ct.c1, ct.c0)), __float2half_ru(fmaf(vb, ct.c1, ct.c0)));
+    __half2 cnt[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) cnt[s] = __float2half2_rn(0.0f);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+#pragma unroll
+        for (int l = s + 1; l < D; ++l) {
+            const __half2 q = __hle2(__habs2(__hsub2(v[s], v[l])), thr);
+            cnt[s] = __hadd2(cnt[s], q);
+            cnt[l] = __hadd2(cnt[l], q);
+        }
+    }
+    // the test with the n_z bound: 0/1 scores count rows here; the continuous
+    // scores first test with n_z >= 0 (no table) and look the bound up only
+    // for the columns that pass that
+    __half2 kneed;
+    if (IND) {
+        kneed = __halves2half2(__float2half_ru(ct.need1 + __low2float(nzi)), __float2half_ru(ct.need1 + __high2float(nzi)));
+    } else {
+        kneed = __halves2half2(__float2half_ru(ct.need1), __float2half_ru(ct.need1));
+    }
+    // bit 10 of each lane of a 1.0/0.0 result, moved to bit s (lane 0) and
+    // bit 16 + s (lane 1)
+    unsigned anc = 0u, acc = 0u;
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const unsigned a = h2bits(__hge2(__habs2(v[s]), ct.ta)) & 0x04000400u;
+        const unsigned c = h2bits(__hge2(cnt[s], kneed));
+        anc |= a >> (10 - s);
+        acc |= (a & c) >> (10 - s);
+    }
+    if (!IND && acc != 0u) {
+        float nza = 0.0f, nzb = 0.0f;
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const unsigned w = h2bits(v[s]);
+            nza += pzlb[(w & 0x7fffu) >> RL0_PZ_SHIFT];
+            nzb += pzlb[(w >> 16 & 0x7fffu) >> RL0_PZ_SHIFT];
+        }
+        kneed = __halves2half2(__float2half_ru(ct.need1 + nza), __float2half_ru(ct.need1 + nzb));
+        acc = 0u;
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const unsigned a = h2bits(__hge2(__habs2(v[s]), ct.ta)) & 0x04000400u;
+            const unsigned c = h2bits(__hge2(cnt[s], kneed));
+            acc |= (a & c) >> (10 - s);
+        }
+    }
+    // a saturated code (|v| = 65504 stands for every larger |r|): no bound
+    const unsigned fa = (va >= 65504.0f) ? anc : acc, fb = (vb >= 65504.0f) ? anc : acc;
+    ma = any_a ? (fa & 0xffffu) : 0u;
+    mb = any_b ? (fb >> 16) : 0u;
+}
+
 // ---------------------------------------------------------------------------
 // H_k (Alg. 2): keep the k entries of largest |x_j|, ties to the smaller j.
 // Radix select of the k-th largest 63-bit key (bits(|x|) << 32 | ~j) among the
