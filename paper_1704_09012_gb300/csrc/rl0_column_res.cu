@@ -442,9 +442,11 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
     last_cta_hk<NT>(a, ctx, hk, suf, &S.last);
 }
 
-// Threads per CTA of each variant (the exact d <= 7 variants fit 64 registers).
+// Threads per CTA of each variant: 512 up to 16 slots (the paired exact
+// variants hold two columns' codes and counts in up to 128 registers; at 64
+// registers the compiler reloads them from shared memory), 256 beyond.
 template <int DMAX, bool EXACT> struct ResNT {
-    static constexpr int value = (EXACT && DMAX <= 7) ? 1024 : (DMAX <= 16 ? 512 : 256);
+    static constexpr int value = DMAX <= 16 ? 512 : 256;
 };
 
 template <int DMAX, bool EXACT>
