@@ -119,9 +119,11 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
             if (gl == 0 && c < nchunks) s_parts[c] = sum;
         }
         bad = __syncthreads_or(bad);
+        // ||r_hat||_1 in k_start's order (lane-strided, then a butterfly)
+        double l1w = 0.0;
+        if (tid < 32) l1w = warp_sum_parts(s_parts, nchunks, lane);
         if (tid == 0) {
-            double l1 = 0.0;
-            for (int c = 0; c < nchunks; ++c) l1 += s_parts[c];
+            const double l1 = l1w;
             S.l1_hat = l1;
             S.stop = (I.stop_rel > 0.0) ? I.stop_rel * l1 : I.stop_level;
             S.status = bad ? RL0_ERR_INVALID_Y : 0;

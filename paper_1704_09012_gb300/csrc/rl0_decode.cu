@@ -41,11 +41,16 @@
 
 
 // r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
-// chunk (one row per thread, blockDim = RL0_ROWS_CHUNK).
-__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const float *src_override, int dst)
+// chunk (one row per thread, blockDim = RL0_ROWS_CHUNK); zero_x: the grid also
+// zeroes the working x (a decode from x_hat = 0).
+__global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const float *src_override, int dst, int zero_x)
 {
     __shared__ double sh[RL0_ROWS_CHUNK];
     const DecodeCtx *ctx = a.ctx;
+    if (zero_x) {
+        float *x = ctx->x;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x) x[j] = 0.0f;
+    }
     const float *src = src_override ? src_override : ctx->y;
     float2 *rz = dst ? a.rz1 : a.rz0;
     double l1 = 0.0;
@@ -70,20 +75,25 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
     }
 }
 
-// Zero the working x.
-__global__ void k_zero_x(KArgs a)
-{
-    float *x = a.ctx->x;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x) x[j] = 0.0f;
-}
-
-// Initial state: r_hat = the source, ||r_hat||_1 from the chunk partials in order.
+// Initial state: r_hat = the source, ||r_hat||_1 from the chunk partials
+// (lane-strided, then a butterfly: the accept step's order).  One warp.  A
+// decode that is done before its first round also takes the final FP64
+// residual norm here (x_hat = 0: the partials of y_hat).
 __global__ void k_start(KArgs a, int round0, int empty_support)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double l1 = 0.0, fin = 0.0;
+    for (int c = lane; c < a.nchunks; c += 32) {
+        l1 += a.l1part[c];
+        fin += a.final_part[c];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        fin += __shfl_xor_sync(0xffffffffu, fin, off);
+    }
+    if (lane != 0) return;
     DecodeState *st = a.st;
-    double l1 = 0.0;
-    for (int c = 0; c < a.nchunks; ++c) l1 += a.l1part[c];
     const int status = st->status;
     st->round = round0;
     st->cur = 0;
@@ -126,6 +136,7 @@ __global__ void k_start(KArgs a, int round0, int empty_support)
         st->skipped = 1;
         st->done = (1 >= a.ctx->nrounds);
     }
+    if (st->done) st->final_l1 = fin;
     if (a.has_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
 }
 
@@ -479,6 +490,17 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
             S.done = 1;
     }
     __syncthreads();
+    if (S.done && t < 32) {
+        // the decode ends here: ||y_hat - A x_hat||_1 from r_hat's FP64 chunk
+        // partials, in k_final_sum's order
+        const double *part = a.final_part + (size_t)S.cur * a.nchunks;
+        double v = 0.0;
+        for (int c = t; c < a.nchunks; c += 32) v += __ldcg(part + c);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (t == 0) S.final_l1 = v;
+        __syncwarp();
+    }
+    __syncthreads();
     if (t < SW) ((unsigned *)st)[t] = ((const unsigned *)&S)[t];
     if (t == 0 && a.has_cond) cudaGraphSetConditional(a.cond, S.done ? 0u : 1u);
 }
@@ -513,12 +535,17 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
             }
             a.bcnt[i] = 0;
         } else {
+            // the count and all 8 slots are read side by side (one L2 trip);
+            // slots past the count are ignored
+            static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
             const int c = a.bcnt[i];
+            const int4 *bq = (const int4 *)(a.bkt + (long long)i * RL0_BUCKET);
+            const int4 b0 = bq[0], b1 = bq[1];
             if (c > 0) {
-                static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
+                const int raw[RL0_BUCKET] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                 int js[RL0_BUCKET];
 #pragma unroll
-                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? a.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
+                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? raw[q] : 0x7fffffff;
                 sort8(js);                              // ascending column order
 #pragma unroll
                 for (int q = 0; q < RL0_BUCKET; ++q)
@@ -700,16 +727,16 @@ struct GraphEntry {
 // done flag and exit.
 #define RL0_ROUNDS_PER_ITER 2
 
-// Kernels one decode graph launches: prologue (3), 3 per round in whole loop
-// iterations, final check (1).
+// Kernels one decode graph launches: prologue (2), 3 per round in whole loop
+// iterations (the step that ends the decode takes the final residual norm).
 int launches_per_decode(int nrounds)
 {
     const int iters = (nrounds + RL0_ROUNDS_PER_ITER - 1) / RL0_ROUNDS_PER_ITER;
-    return 3 + 3 * RL0_ROUNDS_PER_ITER * iters + 1;
+    return 2 + 3 * RL0_ROUNDS_PER_ITER * iters;
 }
 
-// The same with every round launched on its own (profile graph, direct launches).
-int launches_unrolled(int nrounds) { return 3 + 3 * nrounds + 1; }
+// The same with every round launched on its own (profile graph).
+int launches_unrolled(int nrounds) { return 2 + 3 * nrounds; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -821,13 +848,12 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             }
             a.cond = h;
             a.has_cond = 1;
-            cudaGraphNode_t n0, n1, n2, nw, n3;
+            cudaGraphNode_t n1, n2, nw;
             const float *nullsrc = nullptr;
             int zero = 0, one = 1;
-            void *ex_rows[2] = {&nullsrc, &zero};
+            void *ex_rows[3] = {&nullsrc, &zero, &one};
             void *ex_start[2] = {&zero, &one};
-            if ((rc = add_kernel_node(g, &n0, nullptr, 0, (void *)k_zero_x, 2 * a.nsm, 256, &a, nullptr, 0))) break;
-            if ((rc = add_kernel_node(g, &n1, &n0, 1, (void *)k_rows_from, a.nchunks, RL0_ROWS_CHUNK, &a, ex_rows, 2)))
+            if ((rc = add_kernel_node(g, &n1, nullptr, 0, (void *)k_rows_from, a.nchunks, RL0_ROWS_CHUNK, &a, ex_rows, 3)))
                 break;
             if ((rc = add_kernel_node(g, &n2, &n1, 1, (void *)k_start, 1, 32, &a, ex_start, 2))) break;
             cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional, {0, 0, 0}, {}, 0};
@@ -843,7 +869,8 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             for (int q = 0; q < RL0_ROUNDS_PER_ITER; ++q) launch_round(a, dmax, indicator, learned, s);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
-            if ((rc = add_kernel_node(g, &n3, &nw, 1, (void *)k_final_sum, 1, 32, &a, nullptr, 0))) break;
+            // the final FP64 residual norm is taken by the step that ends the
+            // decode (k_start or the accept step): no epilogue kernel
         } while (0);
         if (rc) { cudaGetLastError(); cudaGraphDestroy(g); return rc; }
         cudaError_t e = cudaGraphInstantiate(&E->exec, g, 0);
@@ -856,8 +883,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         return cudaEventRecordWithFlags(E->events[idx], s, cudaEventRecordExternal);
     };
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0, 1);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < nrounds && e == cudaSuccess; ++r) {
@@ -870,7 +896,6 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         if (e == cudaSuccess) e = mark(4 * r + 3);
     }
     if (e == cudaSuccess) e = mark(4 * nrounds);
-    k_final_sum<<<1, 32, 0, s>>>(a);
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return rl0_cuda_err(e); }
     if (e2 != cudaSuccess) return rl0_cuda_err(e2);
@@ -1064,8 +1089,7 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
     const int dmax = dmax_of(A->d);
     cudaEvent_t *ev = (cudaEvent_t *)A->events;
     if (stats) CK(cudaEventRecord(ev[0], s));
-    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0, 1);
     k_start<<<1, 32, 0, s>>>(a, 0, 0);
     CK(cudaGetLastError());
     // the device set the stop level (noiseless: tol ||y_hat||_1); keep it
@@ -1078,7 +1102,7 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
     std::vector<int> pairs;
     std::vector<std::pair<int, float>> supp;
     std::vector<float> vals;
-    int launches = 3;
+    int launches = 2;
     for (int r = 0; r < H->st.round && r < RL0_MAX_ROUNDS; ++r) H->kprior[r] = kprior;   // recorded rounds
     for (int r = H->st.round; r < R.nrounds && !H->st.done; ++r) {
         H->kprior[r] = kprior;
@@ -1441,7 +1465,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     const KArgs a = make_args(A);
     k_copy_f<<<2 * a.nsm, 256, 0, s>>>(xhat_dev, xp_dev, a.n);
-    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0, 0);
     k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
     k_list_count_from_support<<<1, 32, 0, s>>>(a);
@@ -1589,8 +1613,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     CK(cudaMemsetAsync(base + L.bcnt, 0, sizeof(int) * (size_t)A->m, s));
 
     const int dmax = dmax_of(A->d);
-    k_zero_x<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, nullptr, 0, 1);
     k_start<<<1, 32, 0, s>>>(a, 0, 1);
     for (int r = 0; r < R.nrounds; ++r) {
         launch_round(a, dmax, R.indicator, R.p.scorer == 1, s);
@@ -1611,7 +1634,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
         stats->final_l1 = l1;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = launches_unrolled(R.nrounds);
+        stats->launches = launches_unrolled(R.nrounds) + 1;      // and k_final_sum
         stats->skipped_rounds = H->st.skipped;
     }
     return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
@@ -1647,7 +1670,7 @@ extern "C" int rl0_candidate_features(const rl0_expander *Ac, const float *y_dev
     int *cnt = (int *)w.list_tmp;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
     const KArgs a = make_args(A);
-    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0);
+    k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0, 0);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
     if (A->d <= 8) {
         if (R.indicator) k_collect<8, true><<<rl0_div_up(a.n, 256), 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
