@@ -75,7 +75,7 @@ typedef struct {
     int     converged;         /* 1 if ||r_hat||_1 <= m sigma_n sqrt(2/pi) at exit           */
     int     status;            /* RL0_OK, or the device-side error of this decode            */
     int64_t support_size;      /* |supp x_hat|                                               */
-    double  final_l1;          /* ||y_hat - A x_hat||_1, recomputed in FP64 at exit          */
+    double  final_l1;          /* ||y_hat - A x_hat||_1 at exit: rows without FP32 rounding  */
     float   ms;                /* device time of the decode (CUDA events), milliseconds      */
     int     hk_rounds;         /* rounds in which H_k had to drop entries                    */
     int     fallback_rounds;   /* rounds whose residual took the full CSR rebuild            */

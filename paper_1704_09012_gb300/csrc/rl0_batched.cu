@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
     __shared__ float s_score[NT], s_w[NT];
     __shared__ unsigned char s_ok[NT];
     __shared__ unsigned s_scan[NT];
-    __shared__ double s_red[NT];
+    __shared__ DF s_red[NT];
     __shared__ double s_parts[RL0_BATCH_MAX_CHUNKS];
     __shared__ HkShared s_hk;
     __shared__ RoundThr s_th;
@@ -108,14 +108,14 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
         int bad = 0;
         for (int cb = 0; cb < nchunks; cb += G) {
             const int c = cb + grp, i = c * RL0_ROWS_CHUNK + gl;
-            double v = 0.0;
+            DF v{0.0f, 0.0f};
             if (c < nchunks && i < m) {
                 const float r = I.y[i];
                 bad |= !isfinite(r);
                 s_rz[i] = make_float2(r, I.indicator ? 0.0f : series_eval(I.pz, r));
-                v = fabs((double)r);
+                v = DF{fabsf(r), 0.0f};
             }
-            const double sum = group_sum_f64(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
+            const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
             if (gl == 0 && c < nchunks) s_parts[c] = sum;
         }
         bad = __syncthreads_or(bad);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                 const bool csr = S.overflow != 0;
                 for (int cb = 0; cb < nchunks; cb += G) {
                     const int c = cb + grp, i = c * RL0_ROWS_CHUNK + gl;
-                    double v = 0.0;
+                    DF v{0.0f, 0.0f};
                     if (c < nchunks && i < m) {
                         float sum = 0.0f;
                         if (csr) {
@@ -255,9 +255,9 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
                         }
                         const float r = I.y[i] - sum;
                         I.rzc[i] = make_float2(r, I.indicator ? 0.0f : series_eval(I.pz, r));
-                        v = fabs((double)r);
+                        v = DF{fabsf(r), 0.0f};
                     }
-                    const double sum = group_sum_f64(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
+                    const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
                     if (gl == 0 && c < nchunks) s_parts[c] = sum;
                 }
                 __syncthreads();
@@ -325,16 +325,16 @@ __global__ void __launch_bounds__(NT) k_decode_batched(const BatchItem *__restri
             __syncthreads();
         }
 
-        // ---- ||y - A x_hat||_1 in FP64 (same chunks and combination as k_final_l1/k_final_sum)
+        // ---- ||y - A x_hat||_1 in FP32 pairs (same chunks and combination as the single decode)
         for (int cb = 0; cb < nchunks; cb += G) {
             const int c = cb + grp, i = c * RL0_ROWS_CHUNK + gl;
-            double v = 0.0;
+            DF v{0.0f, 0.0f};
             if (c < nchunks && i < m) {
-                double acc = (double)I.y[i];
-                for (int p = I.rowptr[i]; p < I.rowptr[i + 1]; ++p) acc -= (double)x[I.colidx[p]];
-                v = fabs(acc);
+                DF acc{I.y[i], 0.0f};
+                for (int p = I.rowptr[i]; p < I.rowptr[i + 1]; ++p) acc = df_sub(acc, x[I.colidx[p]]);
+                v = df_abs(acc);
             }
-            const double sum = group_sum_f64(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
+            const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
             if (gl == 0 && c < nchunks) s_parts[c] = sum;
         }
         __syncthreads();

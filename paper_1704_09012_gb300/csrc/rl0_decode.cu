@@ -13,7 +13,8 @@
 //                 key (|x_j| bits, ~j): ties go to the smaller j);
 //   scatter       the support's (row, column) pairs into per-row buckets;
 //   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32 (and
-//                 the same sum in FP64 for the final residual check), with
+//                 the same sum in FP32 pairs, about 48 bits, for the final
+//                 residual check), with
 //                 p_z(r_i), the residual code, and l1 partials over fixed
 //                 256-row chunks (a CSR(A^T) pass replaces it when a bucket
 //                 overflows).  The launch's last CTA accepts the round if
@@ -40,12 +41,12 @@
     } while (0)
 
 
-// r source -> rz[dst] = (r, p_z(r)), FP64 l1 partial of each RL0_ROWS_CHUNK-row
+// r source -> rz[dst] = (r, p_z(r)), the l1 partial (FP32 pairs, stored in FP64) of each RL0_ROWS_CHUNK-row
 // chunk (one row per thread, blockDim = RL0_ROWS_CHUNK); zero_x: the grid also
 // zeroes the working x (a decode from x_hat = 0).
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const float *src_override, int dst, int zero_x)
 {
-    __shared__ double sh[RL0_ROWS_CHUNK];
+    __shared__ DF sh[RL0_ROWS_CHUNK];
     const DecodeCtx *ctx = a.ctx;
     if (zero_x) {
         float *x = ctx->x;
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
     }
     const float *src = src_override ? src_override : ctx->y;
     float2 *rz = dst ? a.rz1 : a.rz0;
-    double l1 = 0.0;
+    DF l1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
     if (i < a.m) {
         const float r = src[i];
@@ -61,12 +62,12 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
         const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
         rz[i] = make_float2(r, z);
         if (a.res_ok) (dst ? a.code1 : a.code0)[i] = residual_code(r);
-        l1 = fabs((double)r);
+        l1 = DF{fabsf(r), 0.0f};
     }
-    const double s = block_sum_f64(l1, sh);
+    const double s = block_sum_df(l1, sh);
     if (threadIdx.x == 0) {
         a.l1part[blockIdx.x] = s;
-        // r = y_hat with x_hat = 0: the FP64 residual-norm partial is the same sum
+        // r = y_hat with x_hat = 0: the final residual-norm partial is the same sum
         if (!src_override) a.final_part[(size_t)dst * a.nchunks + blockIdx.x] = s;
     }
     if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows not yet zero
@@ -77,8 +78,8 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
 
 // Initial state: r_hat = the source, ||r_hat||_1 from the chunk partials
 // (lane-strided, then a butterfly: the accept step's order).  One warp.  A
-// decode that is done before its first round also takes the final FP64
-// residual norm here (x_hat = 0: the partials of y_hat).
+// decode that is done before its first round also takes the final residual
+// norm here (x_hat = 0: the partials of y_hat).
 __global__ void k_start(KArgs a, int round0, int empty_support)
 {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
@@ -491,7 +492,7 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
     }
     __syncthreads();
     if (S.done && t < 32) {
-        // the decode ends here: ||y_hat - A x_hat||_1 from r_hat's FP64 chunk
+        // the decode ends here: ||y_hat - A x_hat||_1 from r_hat's chunk
         // partials, in k_final_sum's order
         const double *part = a.final_part + (size_t)S.cur * a.nchunks;
         double v = 0.0;
@@ -507,7 +508,7 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
 
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
 {
-    __shared__ double2 sh2[RL0_ROWS_CHUNK];
+    __shared__ DF sha[RL0_ROWS_CHUNK], shb[RL0_ROWS_CHUNK];
     __shared__ unsigned s_scan[RL0_ROWS_CHUNK];
     __shared__ int s_last;
     DecodeState *st = a.st;
@@ -522,16 +523,16 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     const DecodeCtx *ctx = a.ctx;
     const float *x = ctx->x;
     float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
-    double l1 = 0.0, f1 = 0.0;
+    DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
     if (i < a.m) {
         float sum = 0.0f;
-        double acc = (double)ctx->y[i];             // the same row in FP64, ascending columns
+        DF acc{ctx->y[i], 0.0f};                   // the same row in FP32 pairs, ascending columns
         if (csr) {
             for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
                 const float xv = x[a.colidx[p]];
                 sum += xv;
-                acc -= (double)xv;
+                acc = df_sub(acc, xv);
             }
             a.bcnt[i] = 0;
         } else {
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
                     if (q < c) {
                         const float xv = x[js[q]];
                         sum += xv;
-                        acc -= (double)xv;
+                        acc = df_sub(acc, xv);
                     }
                 a.bcnt[i] = 0;
             }
@@ -561,17 +562,17 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
         const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
         rz[i] = make_float2(r, z);
         if (a.res_ok) (st->cur ? a.code0 : a.code1)[i] = residual_code(r);
-        l1 = fabs((double)r);
-        f1 = fabs(acc);
+        l1 = DF{fabsf(r), 0.0f};
+        f1 = df_abs(acc);
     }
-    // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 with every step FP64
-    const double2 s2 = block_sum2_f64(l1, f1, sh2);
+    // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 without FP32 rounding
+    const double2 s2 = block_sum2_df(l1, f1, sha, shb);
     if (threadIdx.x == 0) {
         a.l1part[blockIdx.x] = s2.x;
         a.final_part[(size_t)(st->cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
     }
     if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows of r' not yet zero
-        const int big = __syncthreads_count(i < a.m && !(fabs(l1) <= (double)ctx->conv_tol));
+        const int big = __syncthreads_count(i < a.m && !(l1.hi <= ctx->conv_tol));
         if (threadIdx.x == 0 && big) atomicAdd(&st->big_cand, (unsigned)big);
     }
     if (no_accept) return;
@@ -586,10 +587,10 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     accept_step<RL0_ROWS_CHUNK>(a, upd, s_scan);
 }
 
-// ||y_hat - A x_hat||_1 with every step in FP64 (the final residual-norm
-// check): the chunk partials of r_hat, formed in FP64 by the kernel that built
-// it (rows summed in ascending column order, 256-row trees), summed in chunk
-// order by one warp.
+// ||y_hat - A x_hat||_1 without FP32 rounding (the final residual-norm check):
+// the chunk partials of r_hat, formed in FP32 pairs by the kernel that built
+// it (rows summed in ascending column order, 256-row trees) and stored in
+// FP64, summed in chunk order by one warp in FP64.
 __global__ void k_final_sum(KArgs a)
 {
     const double *part = a.final_part + (size_t)a.st->cur * a.nchunks;
@@ -603,29 +604,28 @@ __global__ void k_final_sum(KArgs a)
 // same FP32 sum as the rebuild) into rz[0], with the chunk l1 partials.
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
 {
-    __shared__ double sh[RL0_ROWS_CHUNK];
+    __shared__ DF sh[RL0_ROWS_CHUNK];
     const DecodeCtx *ctx = a.ctx;
     const float *x = ctx->x;
-    double l1 = 0.0;
+    DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    double f1 = 0.0;
     if (i < a.m) {
         float sum = 0.0f;
-        double acc = (double)ctx->y[i];
+        DF acc{ctx->y[i], 0.0f};
         for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
             const float xv = x[a.colidx[p]];
             sum += xv;
-            acc -= (double)xv;
+            acc = df_sub(acc, xv);
         }
         const float r = ctx->y[i] - sum;
         if (!isfinite(ctx->y[i])) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
         a.rz0[i] = make_float2(r, ctx->indicator ? 0.0f : series_eval(ctx->pz, r));
         if (a.res_ok) a.code0[i] = residual_code(r);
-        l1 = fabs((double)r);
-        f1 = fabs(acc);
+        l1 = DF{fabsf(r), 0.0f};
+        f1 = df_abs(acc);
     }
-    const double s = block_sum_f64(l1, sh);
-    const double sf = block_sum_f64(f1, sh);
+    const double s = block_sum_df(l1, sh);
+    const double sf = block_sum_df(f1, sh);
     if (threadIdx.x == 0) {
         a.l1part[blockIdx.x] = s;
         a.final_part[blockIdx.x] = sf;
@@ -807,7 +807,8 @@ void launch_round(const KArgs &a, int dmax, int indicator, int learned, cudaStre
 // The round loop as a graph.  Normal decodes: prologue kernels, then a WHILE
 // conditional node whose body is RL0_ROUNDS_PER_ITER rounds (the rebuild's
 // last CTA clears the condition once the decode is done; a round after that
-// only sees the done flag), then the FP64 residual check.  Profile decodes:
+// only sees the done flag); the step that ends the decode takes the final
+// residual norm.  Profile decodes:
 // the rounds unrolled, with event-record nodes around each kernel group (event
 // nodes are not allowed in a conditional body).
 int add_kernel_node(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep, void *func,
@@ -869,7 +870,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
             for (int q = 0; q < RL0_ROUNDS_PER_ITER; ++q) launch_round(a, dmax, indicator, learned, s);
             cudaGraph_t body_out = nullptr;
             if (cudaStreamEndCapture(s, &body_out) != cudaSuccess) { rc = RL0_ERR_CUDA; break; }
-            // the final FP64 residual norm is taken by the step that ends the
+            // the final residual norm is taken by the step that ends the
             // decode (k_start or the accept step): no epilogue kernel
         } while (0);
         if (rc) { cudaGetLastError(); cudaGraphDestroy(g); return rc; }

@@ -42,11 +42,119 @@ __device__ __forceinline__ float series_eval(const Series &S, float w)
                        : (fabsf(w) > S.cut ? 0.0f : p);   // below 2^-40 beyond the cut
 }
 
-// Fixed-shape FP64 tree over `n` consecutive threads starting at `base`
-// (n a power of two, 64 <= n): sh[t] += sh[t + off] for off = n/2 .. 1.  The
-// levels off >= 32 go through shared memory, the last five through warp
-// shuffles in the group's first warp: the same additions in the same order.
-// Every thread of the block must call it (it synchronises the block).
+// ---------------------------------------------------------------------------
+// Residual norms in FP32 pairs.  A value is hi + lo with |lo| <= ulp(hi)/2
+// (about 48 significant bits), added with error-free transformations: TwoSum
+// (Knuth, TAOCP vol. 2, 4.2.2) makes s + e = a + b exactly.  Everything runs
+// on the FP32 pipes (this GPU's FP64 rate is a small fraction of its FP32
+// rate); a sum is converted to FP64 once, exactly, as (double)hi + (double)lo.
+// The compiler keeps these steps as written: no FMA pattern, no reassociation.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+
+// a + b, both normalised
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi);
+    return df_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+// a - x for an FP32 x
+__device__ __forceinline__ DF df_sub(DF a, float x)
+{
+    const DF s = df_two_sum(a.hi, -x);
+    return df_two_sum(s.hi, s.lo + a.lo);
+}
+
+__device__ __forceinline__ DF df_abs(DF a) { return (a.hi < 0.0f) ? DF{-a.hi, -a.lo} : a; }
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ DF df_shfl_down(DF v, int off)
+{
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+
+// Fixed-shape tree over `n` consecutive threads (n a power of two, 64 <= n):
+// sh[t] += sh[t + off] for off = n/2 .. 1, the levels off >= 32 through shared
+// memory, the last five through warp shuffles in the group's first warp: the
+// same additions in the same order wherever it runs.  Every thread of the
+// block must call it (it synchronises the block).  Returns the sum in FP64.
+__device__ __forceinline__ double group_sum_df(DF v, DF *sh, int lane, int n)
+{
+    sh[lane] = v;
+    __syncthreads();
+    for (int off = n >> 1; off >= 32; off >>= 1) {
+        if (lane < off) sh[lane] = df_add(sh[lane], sh[lane + off]);
+        __syncthreads();
+    }
+    DF r{0.0f, 0.0f};
+    if (lane < 32) {
+        r = sh[lane];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const DF u = df_shfl_down(r, off);
+            if (lane < off) r = df_add(r, u);
+        }
+        if (lane == 0) sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return df_to_double(r);
+}
+
+__device__ __forceinline__ double block_sum_df(DF v, DF *sh)
+{
+    return group_sum_df(v, sh, threadIdx.x, blockDim.x);
+}
+
+// Two block_sum_df trees in one pass (the same additions in the same order).
+__device__ __forceinline__ double2 block_sum2_df(DF a, DF b, DF *sha, DF *shb)
+{
+    const int t = threadIdx.x, n = blockDim.x;
+    sha[t] = a;
+    shb[t] = b;
+    __syncthreads();
+    for (int off = n >> 1; off >= 32; off >>= 1) {
+        if (t < off) {
+            sha[t] = df_add(sha[t], sha[t + off]);
+            shb[t] = df_add(shb[t], shb[t + off]);
+        }
+        __syncthreads();
+    }
+    DF ra{0.0f, 0.0f}, rb{0.0f, 0.0f};
+    if (t < 32) {
+        ra = sha[t];
+        rb = shb[t];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const DF ua = df_shfl_down(ra, off), ub = df_shfl_down(rb, off);
+            if (t < off) {
+                ra = df_add(ra, ua);
+                rb = df_add(rb, ub);
+            }
+        }
+        if (t == 0) {
+            sha[0] = ra;
+            shb[0] = rb;
+        }
+    }
+    __syncthreads();
+    const double2 r = make_double2(df_to_double(sha[0]), df_to_double(shb[0]));
+    __syncthreads();
+    return r;
+}
+
+// The same tree in FP64 (the MLP's training loss).
 __device__ __forceinline__ double group_sum_f64(double v, double *sh, int lane, int n)
 {
     sh[lane] = v;
@@ -64,45 +172,6 @@ __device__ __forceinline__ double group_sum_f64(double v, double *sh, int lane, 
             if (lane < off) r += u;
         }
         if (lane == 0) sh[0] = r;
-    }
-    __syncthreads();
-    r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ double block_sum_f64(double v, double *sh)
-{
-    return group_sum_f64(v, sh, threadIdx.x, blockDim.x);
-}
-
-// Two block_sum_f64 trees in one pass (the same additions in the same order).
-__device__ __forceinline__ double2 block_sum2_f64(double a, double b, double2 *sh)
-{
-    const int t = threadIdx.x, n = blockDim.x;
-    sh[t] = make_double2(a, b);
-    __syncthreads();
-    for (int off = n >> 1; off >= 32; off >>= 1) {
-        if (t < off) {
-            const double2 u = sh[t + off];
-            sh[t].x += u.x;
-            sh[t].y += u.y;
-        }
-        __syncthreads();
-    }
-    double2 r = make_double2(0.0, 0.0);
-    if (t < 32) {
-        r = sh[t];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ux = __shfl_down_sync(0xffffffffu, r.x, off);
-            const double uy = __shfl_down_sync(0xffffffffu, r.y, off);
-            if (t < off) {
-                r.x += ux;
-                r.y += uy;
-            }
-        }
-        if (t == 0) sh[0] = r;
     }
     __syncthreads();
     r = sh[0];
