@@ -37,9 +37,9 @@ def _A(rows, m):
     return sp.csr_matrix((np.ones(n * d), (rows.ravel(), np.repeat(np.arange(n), d))), shape=(m, n))
 
 
-def _problem(n, m, k, d, sigma_n, seed):
+def _problem(n, m, k, d, sigma_n, seed, sigma_s=1.0):
     """Instance from the generator, y_hat computed by the oracle in FP64 and rounded to FP32."""
-    I = gm.instance(n, m, k, d, sigma_n, seed)
+    I = gm.instance(n, m, k, d, sigma_n, seed, sigma_s=sigma_s)
     y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
     return I, y.astype(np.float32)
 
@@ -201,6 +201,8 @@ def test_decode_small_config_matches_oracle(rl0, quantised, seed):
 
 
 @pytest.mark.parametrize("cfg", [dict(n=5003, m=1201, k=110, d=7, sigma_n=2e-3),      # ragged tail
+                                 dict(n=4100, m=1100, k=90, d=6, sigma_n=1e-3),        # paired FP16 bound, d = 6
+                                 dict(n=4100, m=1100, k=70, d=8, sigma_n=1e-3),        # paired FP16 bound, d = 8
                                  dict(n=20000, m=3000, k=250, d=15, sigma_n=1e-3),     # d = 15
                                  dict(n=6000, m=1500, k=100, d=20, sigma_n=1e-3),      # d > 16
                                  dict(n=3000, m=900, k=60, d=7, sigma_n=0.0)])         # noiseless
@@ -211,6 +213,22 @@ def test_decode_other_shapes_match_oracle(rl0, cfg, quantised):
     assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
     assert _rel(xg, xo) <= XTOL
     assert st["accepted_rounds"] == sto["accepted_rounds"]
+
+
+@pytest.mark.parametrize("d", [7, 5])
+@pytest.mark.parametrize("quantised", [False, True])
+def test_decode_with_saturated_codes_matches_oracle(rl0, d, quantised):
+    # sigma_s = 3e4: some residuals exceed the largest FP16 magnitude (65504), so the
+    # column kernel cannot bound their columns from the 16-bit codes and takes every
+    # anchor of such a column to the exact test (d = 7: the paired FP16 bound; d = 5:
+    # the scalar one).  The decode must be the oracle's all the same.
+    I, y32 = _problem(4096, 1024, 80, d, 30.0, 9, sigma_s=3e4)
+    assert np.abs(y32).max() > 65504
+    A, xg, st, xo, sto, _ = _decode_both(rl0, I, y32, quantised=quantised, sigma_s=3e4)
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert _rel(xg, xo) <= XTOL
+    assert st["accepted_rounds"] == sto["accepted_rounds"]
+    assert st["accepted_rounds"] > 0
 
 
 def test_decode_edge_cases(rl0):
