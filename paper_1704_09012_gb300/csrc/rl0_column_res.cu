@@ -137,15 +137,14 @@ __device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsu
     return r;
 }
 
+// One round's column score up to the CTA's commit (load, stream, resolve).
 // DMAX slots per column; EXACT: d == DMAX (the slot guards fold away).
 template <int DMAX, bool IND, bool EXACT, int NT>
-__global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
+__device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm)
 {
     // exact d <= 8: two columns per thread in FP16 lanes (code_candidates2)
     constexpr bool PAIRED = EXACT && DMAX <= 8;
-    extern __shared__ __align__(16) unsigned char dsm[];
     DecodeState *st = a.st;
-    if (st->done) return;
     const DecodeCtx *ctx = a.ctx;
     const int n = a.n, tid = threadIdx.x;
     const int d = EXACT ? DMAX : a.d;
@@ -436,10 +435,19 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
         if (fresh) a.list[S.fbase + (pf & 0xffffu)] = j;
         __syncthreads();                           // the scratch is reused by the next batch
     }
+}
+
+template <int DMAX, bool IND, bool EXACT, int NT>
+__global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    if (a.st->done) return;
+    column_phase<DMAX, IND, EXACT, NT>(a, dsm);
     // the codes are no longer needed: their bytes become H_k's scratch
+    ResShared &S = *(ResShared *)(dsm + a.res_s_off);
     HkShared &hk = *(HkShared *)dsm;
     unsigned *suf = (unsigned *)(dsm + ((sizeof(HkShared) + 15) & ~(size_t)15));
-    last_cta_hk<NT>(a, ctx, hk, suf, &S.last);
+    last_cta_hk<NT>(a, a.ctx, hk, suf, &S.last);
 }
 
 // Threads per CTA of each variant: 512 up to 16 slots (the paired exact

@@ -357,154 +357,10 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a)
 {
     DecodeState *st = a.st;
     if (st->done || st->upd_count == 0) return;
-    const float *x = a.ctx->x;
-    const unsigned total = st->list_count;
-    const int d = a.d;
-    const long long work = (long long)total * d;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < work;
-         w += (long long)gridDim.x * blockDim.x) {
-        const unsigned e = (unsigned)(w / d);
-        const int s = (int)(w % d);
-        const int j = a.list[e];
-        if (x[j] == 0.0f) continue;
-        const int row = a.rows_cm[(long long)j * d + s];
-        const int slot = atomicAdd(&a.bcnt[row], 1);
-        if (slot < RL0_BUCKET) a.bkt[(long long)row * RL0_BUCKET + slot] = j;
-        else a.st->overflow = 1;
-    }
+    scatter_items(a, st->list_count, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                  (long long)gridDim.x * blockDim.x);
 }
 
-
-// ---------------------------------------------------------------------------
-// Accept / undo and round control, run by one CTA of NT threads: the rebuild's
-// last CTA, or its CTA 0 when the round changed nothing.
-// ---------------------------------------------------------------------------
-template <int NT>
-__device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
-{
-    // The state is read once into shared memory (warp 0, one word per lane,
-    // through L2: other CTAs of this launch wrote to it), decided on there,
-    // and written back once, so thread 0's decisions wait on no global loads.
-    constexpr int SW = sizeof(DecodeState) / 4;
-    static_assert(sizeof(DecodeState) % 4 == 0 && SW <= 32, "one word per lane of warp 0");
-    __shared__ DecodeState S;
-    __shared__ double s_l1;
-    __shared__ int s_acc;
-    DecodeState *st = a.st;
-    const int t = threadIdx.x;
-    const DecodeCtx *ctx = a.ctx;
-    float *x = ctx->x;
-    if (t < 32) {
-        if (t < SW) ((unsigned *)&S)[t] = __ldcg((const unsigned *)st + t);
-        double v = 0.0;
-        if (upd > 0) {
-            // ||r||_1 of the candidate: chunk partials combined in a fixed order
-            for (int c = t; c < a.nchunks; c += 32) v += __ldcg(a.l1part + c);
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        }
-        __syncwarp();
-        if (t == 0) {
-            S.rb_done = 0u;                        // the rebuild's last-CTA count starts over
-            s_l1 = v;
-            s_acc = (upd > 0) ? (ctx->always_accept ? 1 : (v < S.l1_hat)) : 0;
-        }
-    }
-    __syncthreads();
-    if (upd > 0) {
-        if (s_acc) {
-            if (S.drop_count > 0 || S.zeroed > 0) {
-                // entries became zero: stable in-place compaction of the list
-                const unsigned total = S.list_count;
-                unsigned out = 0;
-                for (unsigned base = 0; base < total; base += NT) {
-                    const unsigned e = base + t;
-                    int j = -1;
-                    unsigned keep = 0;
-                    if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
-                    shu[t] = keep;
-                    __syncthreads();
-                    for (int off = 1; off < NT; off <<= 1) {
-                        const unsigned w = (t >= off) ? shu[t - off] : 0u;
-                        __syncthreads();
-                        shu[t] += w;
-                        __syncthreads();
-                    }
-                    const unsigned incl = shu[t];
-                    const unsigned blk = shu[NT - 1];
-                    __syncthreads();
-                    if (keep) a.list[out + incl - 1] = j;
-                    out += blk;
-                    __syncthreads();
-                }
-                if (t == 0) S.list_count = out;
-            }
-            if (t == 0) {
-                S.shat_count = S.list_count;
-                S.nnz = (unsigned)((int)S.nnz + S.nnz_delta - (int)S.drop_count);
-                S.cur ^= 1;
-                S.l1_hat = s_l1;
-                S.accepted_rounds += 1;
-            }
-        } else {
-            const unsigned nd = S.drop_count;
-            for (unsigned e = t; e < nd; e += NT) x[a.dlog[e].j] = a.dlog[e].old;
-            __syncthreads();
-            for (unsigned e = t; e < upd; e += NT) x[a.ulog[e].j] = a.ulog[e].old;
-            if (t == 0) S.list_count = S.shat_count;
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        const int round = S.round;
-        const double l1n = (upd > 0) ? s_l1 : S.l1_hat;
-        if (ctx->want_log && round < RL0_MAX_ROUNDS) {
-            RoundLog L;
-            L.l1_candidate = l1n;
-            L.l1_hat = S.l1_hat;
-            L.accepted = s_acc;
-            L.updated = (int)upd;
-            L.support = (int)S.nnz;
-            L.hk_dropped = (int)S.drop_count;
-            a.rlog[round] = L;
-        }
-        if (upd > 0 && S.drop_count > 0) S.hk_rounds += 1;
-        if (upd > 0 && S.overflow) S.fallback_rounds += 1;
-        S.upd_count = 0;
-        S.drop_count = 0;
-        S.overflow = 0;
-        S.nnz_delta = 0;
-        S.zeroed = 0;
-        S.round = round + 1;
-        S.rounds_run += 1;
-        S.iters += 1;
-        S.l1_new = l1n;
-        if (ctx->always_accept) {
-            // Alg. 1: every iteration is kept; it ends when one changes nothing
-            if (upd > 0) S.big_hat = S.big_cand;
-            S.converged = (S.big_hat == 0);
-            if (upd == 0) S.done = 1;
-        } else {
-            S.converged = (S.l1_hat <= ctx->stop_level);
-        }
-        S.big_cand = 0;
-        if (S.converged || S.round >= ctx->nrounds || S.iters > (unsigned)ctx->nrounds || S.status != 0)
-            S.done = 1;
-    }
-    __syncthreads();
-    if (S.done && t < 32) {
-        // the decode ends here: ||y_hat - A x_hat||_1 from r_hat's chunk
-        // partials, in k_final_sum's order
-        const double *part = a.final_part + (size_t)S.cur * a.nchunks;
-        double v = 0.0;
-        for (int c = t; c < a.nchunks; c += 32) v += __ldcg(part + c);
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (t == 0) S.final_l1 = v;
-        __syncwarp();
-    }
-    __syncthreads();
-    if (t < SW) ((unsigned *)st)[t] = ((const unsigned *)&S)[t];
-    if (t == 0 && a.has_cond) cudaGraphSetConditional(a.cond, S.done ? 0u : 1u);
-}
 
 __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
 {
@@ -521,55 +377,15 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     }
     const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
     const DecodeCtx *ctx = a.ctx;
-    const float *x = ctx->x;
-    float2 *rz = st->cur ? a.rz0 : a.rz1;          // the candidate buffer
+    const int cur = st->cur;
     DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    if (i < a.m) {
-        float sum = 0.0f;
-        DF acc{ctx->y[i], 0.0f};                   // the same row in FP32 pairs, ascending columns
-        if (csr) {
-            for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
-                const float xv = x[a.colidx[p]];
-                sum += xv;
-                acc = df_sub(acc, xv);
-            }
-            a.bcnt[i] = 0;
-        } else {
-            // the count and all 8 slots are read side by side (one L2 trip);
-            // slots past the count are ignored
-            static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
-            const int c = a.bcnt[i];
-            const int4 *bq = (const int4 *)(a.bkt + (long long)i * RL0_BUCKET);
-            const int4 b0 = bq[0], b1 = bq[1];
-            if (c > 0) {
-                const int raw[RL0_BUCKET] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                int js[RL0_BUCKET];
-#pragma unroll
-                for (int q = 0; q < RL0_BUCKET; ++q) js[q] = (q < c) ? raw[q] : 0x7fffffff;
-                sort8(js);                              // ascending column order
-#pragma unroll
-                for (int q = 0; q < RL0_BUCKET; ++q)
-                    if (q < c) {
-                        const float xv = x[js[q]];
-                        sum += xv;
-                        acc = df_sub(acc, xv);
-                    }
-                a.bcnt[i] = 0;
-            }
-        }
-        const float r = ctx->y[i] - sum;
-        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
-        rz[i] = make_float2(r, z);
-        if (a.res_ok) (st->cur ? a.code0 : a.code1)[i] = residual_code(r);
-        l1 = DF{fabsf(r), 0.0f};
-        f1 = df_abs(acc);
-    }
+    if (i < a.m) rebuild_row(a, ctx, i, csr, cur, l1, f1);
     // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 without FP32 rounding
     const double2 s2 = block_sum2_df(l1, f1, sha, shb);
     if (threadIdx.x == 0) {
         a.l1part[blockIdx.x] = s2.x;
-        a.final_part[(size_t)(st->cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
+        a.final_part[(size_t)(cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
     }
     if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows of r' not yet zero
         const int big = __syncthreads_count(i < a.m && !(l1.hi <= ctx->conv_tol));

@@ -117,33 +117,33 @@ __device__ __forceinline__ double block_sum_df(DF v, DF *sh)
     return group_sum_df(v, sh, threadIdx.x, blockDim.x);
 }
 
-// Two block_sum_df trees in one pass (the same additions in the same order).
-__device__ __forceinline__ double2 block_sum2_df(DF a, DF b, DF *sha, DF *shb)
+// Two group_sum_df trees in one pass (the same additions in the same order),
+// over groups of n consecutive threads; sha/shb point at the group's n slots.
+__device__ __forceinline__ double2 group_sum2_df(DF a, DF b, DF *sha, DF *shb, int lane, int n)
 {
-    const int t = threadIdx.x, n = blockDim.x;
-    sha[t] = a;
-    shb[t] = b;
+    sha[lane] = a;
+    shb[lane] = b;
     __syncthreads();
     for (int off = n >> 1; off >= 32; off >>= 1) {
-        if (t < off) {
-            sha[t] = df_add(sha[t], sha[t + off]);
-            shb[t] = df_add(shb[t], shb[t + off]);
+        if (lane < off) {
+            sha[lane] = df_add(sha[lane], sha[lane + off]);
+            shb[lane] = df_add(shb[lane], shb[lane + off]);
         }
         __syncthreads();
     }
     DF ra{0.0f, 0.0f}, rb{0.0f, 0.0f};
-    if (t < 32) {
-        ra = sha[t];
-        rb = shb[t];
+    if (lane < 32) {
+        ra = sha[lane];
+        rb = shb[lane];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const DF ua = df_shfl_down(ra, off), ub = df_shfl_down(rb, off);
-            if (t < off) {
+            if (lane < off) {
                 ra = df_add(ra, ua);
                 rb = df_add(rb, ub);
             }
         }
-        if (t == 0) {
+        if (lane == 0) {
             sha[0] = ra;
             shb[0] = rb;
         }
@@ -152,6 +152,11 @@ __device__ __forceinline__ double2 block_sum2_df(DF a, DF b, DF *sha, DF *shb)
     const double2 r = make_double2(df_to_double(sha[0]), df_to_double(shb[0]));
     __syncthreads();
     return r;
+}
+
+__device__ __forceinline__ double2 block_sum2_df(DF a, DF b, DF *sha, DF *shb)
+{
+    return group_sum2_df(a, b, sha, shb, threadIdx.x, blockDim.x);
 }
 
 // The same tree in FP64 (the MLP's training loss).
@@ -185,6 +190,26 @@ __device__ __forceinline__ double warp_sum_parts(const double *parts, int nparts
 {
     double v = 0.0;
     for (int c = lane; c < nparts; c += 32) v += parts[c];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// The same sum over chunk partials in global memory written in this launch
+// (read through L2), four loads in flight per lane; the additions are those
+// of warp_sum_parts, in the same order.
+__device__ __forceinline__ double warp_sum_parts_l2(const double *parts, int nparts, int lane)
+{
+    double v = 0.0;
+    int c = lane;
+    for (; c + 96 < nparts; c += 128) {
+        const double p0 = __ldcg(parts + c), p1 = __ldcg(parts + c + 32), p2 = __ldcg(parts + c + 64),
+                     p3 = __ldcg(parts + c + 96);
+        v += p0;
+        v += p1;
+        v += p2;
+        v += p3;
+    }
+    for (; c < nparts; c += 32) v += __ldcg(parts + c);
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
