@@ -538,10 +538,10 @@ struct GraphEntry {
 };
 
 // Rounds per iteration of the graph's WHILE loop: one iteration of the
-// conditional node costs about as much as a kernel launch, so two rounds share
-// one; after an odd number of rounds the second round's kernels only see the
-// done flag and exit.
-#define RL0_ROUNDS_PER_ITER 2
+// conditional node costs about 4 us, a round whose kernels only see the done
+// flag about 2 us per kernel; three rounds per iteration measured best on 5-,
+// 6- and 39-round decodes (2 and 4 were slower).
+#define RL0_ROUNDS_PER_ITER 3
 
 // Kernels one decode graph launches: prologue (2), 3 per round in whole loop
 // iterations (the step that ends the decode takes the final residual norm).
