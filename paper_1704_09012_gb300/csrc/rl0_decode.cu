@@ -393,12 +393,10 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     }
     if (no_accept) return;
     // ---- the launch's last CTA accepts or undoes the round
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&st->rb_done, 1u) == gridDim.x - 1u);
+    if (threadIdx.x == 0) s_last = (cta_ticket(&st->rb_done) == gridDim.x - 1u);
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     if (threadIdx.x == 0) st->rb_done = 0u;
     accept_step<RL0_ROWS_CHUNK>(a, upd, s_scan);
 }

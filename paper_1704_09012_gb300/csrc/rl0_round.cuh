@@ -78,6 +78,18 @@ __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *c
     }
 }
 
+// A CTA's ticket at the end of a launch: after the block barrier, thread 0
+// adds one with release and acquire semantics at GPU scope, so the CTA's
+// writes are visible to whichever CTA draws the last ticket, and that CTA
+// (after its next block barrier) sees every other CTA's.  Returns the count
+// before this CTA's ticket.
+__device__ __forceinline__ unsigned cta_ticket(unsigned *ctr)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    return old;
+}
+
 // The launch's last CTA applies H_k when |supp x'| > k (state read past L1,
 // since other CTAs updated it during this launch).  hk and suf are scratch of
 // that CTA; *last is a shared flag.
@@ -85,12 +97,10 @@ template <int NT>
 __device__ __forceinline__ void last_cta_hk(const KArgs &a, const DecodeCtx *ctx, HkShared &hk, unsigned *suf,
                                             int *last)
 {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) *last = (atomicAdd(&a.st->col_done, 1u) == gridDim.x - 1u);
+    if (threadIdx.x == 0) *last = (cta_ticket(&a.st->col_done) == gridDim.x - 1u);
     __syncthreads();
     if (!*last) return;
-    __threadfence();
     DecodeState *stw = a.st;
     const unsigned upd = __ldcg(&stw->upd_count);
     const long long nnz = (long long)__ldcg(&stw->nnz) + __ldcg(&stw->nnz_delta);
