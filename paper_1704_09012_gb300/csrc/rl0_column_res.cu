@@ -6,11 +6,13 @@
 //   load     the CTA copies the 16-bit codes of all m rows (and the p_z bound
 //            table) into shared memory with bulk asynchronous copies
 //            (cp.async.bulk + mbarrier), 2 bytes per row;
-//   stream   each thread takes one column per tile of NT columns, reads its d
-//            row ids from HBM (one coalesced 4-byte load per slot; the next
-//            tile's are prefetched) and its d codes from shared memory, and
-//            bounds the column's anchors with code_candidates; no thread
-//            waits on another; a column that survives (about 1%) is listed
+//   stream   each thread takes one column per tile of NT columns (two, j and
+//            j + NT, per tile of 2 NT for exact d <= 8), reads their d row ids
+//            (one coalesced 4-byte load per slot; the next tile's are
+//            prefetched) and their codes from shared memory, and bounds their
+//            anchors with code_candidates (code_candidates2: both columns in
+//            the FP16 lanes of half2 registers); no thread waits on another;
+//            a column that survives (about 1%) is listed
 //            with its candidate slots: the first res_qcap of a CTA in shared
 //            memory, where asynchronous copies (cp.async) fetch its FP32
 //            (r, p_z) and x_j while the stream goes on, the rest in the CTA's
@@ -23,8 +25,8 @@
 //            slot) sums them, and each column takes its highest passing slot
 //            (the last passing anchor in row order); the CTA then commits with
 //            one global atomic per counter;
-//   H_k      the launch's last CTA applies H_k, its scratch in the bytes that
-//            held the codes.
+//   H_k      the launch's last CTA (an acquire-release ticket) applies H_k
+//            when |supp x'| > k, its scratch in the bytes that held the codes.
 // The resolve runs the arithmetic of k_column_score in the same order, so
 // both kernels give the same x'.
 #include <algorithm>

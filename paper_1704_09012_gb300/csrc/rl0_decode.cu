@@ -14,10 +14,9 @@
 //   scatter       the support's (row, column) pairs into per-row buckets;
 //   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32 (and
 //                 the same sum in FP32 pairs, about 48 bits, for the final
-//                 residual check), with
-//                 p_z(r_i), the residual code, and l1 partials over fixed
-//                 256-row chunks (a CSR(A^T) pass replaces it when a bucket
-//                 overflows).  The launch's last CTA accepts the round if
+//                 residual check), with p_z(r_i), the residual code, and l1
+//                 partials over fixed 256-row chunks (a CSR(A^T) pass replaces
+//                 it when a bucket overflows).  The launch's last CTA accepts the round if
 //                 ||r||_1 < ||r_hat||_1 or undoes it, advances t and clears
 //                 the graph's loop condition when the decode is done.
 // No float atomics anywhere: every sum has a fixed order, so results do not

@@ -1,7 +1,9 @@
 // rl0_round.cuh -- pieces of one Robust-l0 round (arXiv 1704.09012,
 // Algorithm 2) shared by the translation units that launch round kernels:
-// the kernel argument block, a column's commit, and the H_k step run by the
-// column kernel's last CTA.  Not part of the ABI.
+// the kernel argument block, a column's commit, the last-CTA ticket and the
+// H_k step run by the column kernel's last CTA, the scatter and the per-row
+// rebuild, and the accept step run by the rebuild's last CTA.  Not part of
+// the ABI.
 #pragma once
 
 #include "rl0_common.cuh"
