@@ -61,6 +61,28 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Each rank decodes its own instance (weak scaling: the work per GPU is fixed)."""
+    return 1000 + rank
+
+
+def max_over_ranks(v, ws, device):
+    """The largest per-rank value over the job (the slowest rank's time); no exchange
+    at one rank.  `device` is where the process group's backend keeps tensors."""
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ws, t_max):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return ws * units_per_rank / t_max
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -396,7 +418,7 @@ def main():
     _b.build()
     n, m, k, d, sn = cfg["n"], cfg["m"], cfg["k"], cfg["d"], cfg["sigma_n"]
     nnz = n * d
-    seed = 1000 + rank
+    seed = rank_seed(rank)
     A = rl0.Expander.random(n, m, d, seed=seed)
     x, _ = gm.draw_signal(n, k, 1.0, seed)
     x_dev = torch.from_numpy(x).cuda()
@@ -433,12 +455,8 @@ def main():
     # throughput counts the rounds that ran kernels (the t = 1 round is only recorded)
     sweep_rounds = stats[-1]["rounds"]
     rounds = sweep_rounds - stats[-1]["skipped_rounds"]
-    if ws > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    units = ws * args.steps * nnz * rounds
-    value = units / t_dev
+    t_dev = max_over_ranks(t_dev, ws, "cuda")
+    value = job_throughput(args.steps * nnz * rounds, ws, t_dev)
     xr = xhat.cpu().numpy().astype(np.float64)
     rel_l1 = float(np.abs(xr - x).sum() / np.abs(x).sum())
 
@@ -456,11 +474,8 @@ def main():
         ev2[s][1].record(stream)
     barrier()
     t_e2e = sum(a.elapsed_time(b) for a, b in ev2) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = ws * args.steps * nnz * rounds / t_e2e
+    t_e2e = max_over_ranks(t_e2e, ws, "cuda")
+    e2e_value = job_throughput(args.steps * nnz * rounds, ws, t_e2e)
 
     # ---- per-kernel device time: event nodes captured around each kernel group
     prof = []
