@@ -367,19 +367,22 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     __shared__ unsigned s_scan[RL0_ROWS_CHUNK];
     __shared__ int s_last;
     DecodeState *st = a.st;
+    const DecodeCtx *ctx = a.ctx;
+    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
+    // the row's inputs do not depend on the state: they load beside it
+    RowIn pre;
+    if (i < a.m) pre = load_row_inputs(a, ctx, i);
     if (st->done) return;
-    const int no_accept = a.ctx->no_accept;
+    const int no_accept = ctx->no_accept;
     const unsigned upd = st->upd_count;
     if (upd == 0) {                                // nothing changed: r = r_hat, only t advances
         if (blockIdx.x == 0 && !no_accept) accept_step<RL0_ROWS_CHUNK>(a, 0u, s_scan);
         return;
     }
     const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
-    const DecodeCtx *ctx = a.ctx;
     const int cur = st->cur;
     DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
-    const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    if (i < a.m) rebuild_row(a, ctx, i, csr, cur, l1, f1);
+    if (i < a.m) rebuild_row(a, ctx, i, csr, cur, l1, f1, &pre);
     // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 without FP32 rounding
     const double2 s2 = block_sum2_df(l1, f1, sha, shb);
     if (threadIdx.x == 0) {

@@ -134,17 +134,37 @@ __device__ __forceinline__ void scatter_items(const KArgs &a, unsigned total, lo
     }
 }
 
+// A row's inputs to the rebuild that do not depend on the decode state: its
+// bucket count, the bucket's 8 slots and y_i (loaded side by side, one L2 trip).
+struct RowIn {
+    int c;
+    int4 b0, b1;
+    float y;
+};
+
+__device__ __forceinline__ RowIn load_row_inputs(const KArgs &a, const DecodeCtx *ctx, int i)
+{
+    RowIn in;
+    in.c = a.bcnt[i];
+    const int4 *bq = (const int4 *)(a.bkt + (long long)i * RL0_BUCKET);
+    in.b0 = bq[0];
+    in.b1 = bq[1];
+    in.y = ctx->y[i];
+    return in;
+}
+
 // ---------------------------------------------------------------------------
 // Rebuild of R rows i[0..R) (has[r]: row r exists): r_i = y_i - sum of x_j
 // over the row in ascending j (FP32), the same sum in FP32 pairs for the final
 // residual check, p_z(r_i) and the residual code into the candidate buffer
 // (cur: the accepted one); l1 = |r_i|, f1 = |that pair sum|.  Every row's
 // loads are issued before any row's stores, so R rows cost one chain of L2
-// trips.  csr: a bucket overflowed, take the rows from CSR(A^T).
+// trips; pre, if not null, holds the rows' inputs already loaded.  csr: a
+// bucket overflowed, take the rows from CSR(A^T).
 // ---------------------------------------------------------------------------
 template <int R>
 __device__ __forceinline__ void rebuild_rows(const KArgs &a, const DecodeCtx *ctx, const int *i, const bool *has,
-                                             bool csr, int cur, DF *l1, DF *f1)
+                                             bool csr, int cur, DF *l1, DF *f1, const RowIn *pre = nullptr)
 {
     static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
     const float *x = ctx->x;
@@ -176,11 +196,11 @@ __device__ __forceinline__ void rebuild_rows(const KArgs &a, const DecodeCtx *ct
             yv[r] = 0.0f;
             int4 b0 = make_int4(0, 0, 0, 0), b1 = b0;
             if (has[r]) {
-                c[r] = a.bcnt[i[r]];
-                const int4 *bq = (const int4 *)(a.bkt + (long long)i[r] * RL0_BUCKET);
-                b0 = bq[0];
-                b1 = bq[1];
-                yv[r] = ctx->y[i[r]];
+                const RowIn in = pre ? pre[r] : load_row_inputs(a, ctx, i[r]);
+                c[r] = in.c;
+                b0 = in.b0;
+                b1 = in.b1;
+                yv[r] = in.y;
             }
             const int raw[RL0_BUCKET] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -220,10 +240,10 @@ __device__ __forceinline__ void rebuild_rows(const KArgs &a, const DecodeCtx *ct
 }
 
 __device__ __forceinline__ void rebuild_row(const KArgs &a, const DecodeCtx *ctx, int i, bool csr, int cur, DF &l1,
-                                            DF &f1)
+                                            DF &f1, const RowIn *pre = nullptr)
 {
     const bool has = true;
-    rebuild_rows<1>(a, ctx, &i, &has, csr, cur, &l1, &f1);
+    rebuild_rows<1>(a, ctx, &i, &has, csr, cur, &l1, &f1, pre);
 }
 
 // ---------------------------------------------------------------------------
