@@ -15,6 +15,7 @@ Function map (paper anchors):
   parallel_l0                              -- Algorithm 1 (Parallel-l0)
 """
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -77,7 +78,9 @@ COLREC_DTYPE = np.dtype([
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # RL0_ORACLE_LIB: a copy of the oracle built elsewhere (the planted-mistake
+        # test runs the pins against mutated copies)
+        path = os.environ.get("RL0_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")

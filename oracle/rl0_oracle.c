@@ -288,6 +288,19 @@ static int orc_series_init(orc_series *S, double lam, double s2, double v_noise,
     return ORC_OK;
 }
 
+/* The two posteriors' series: which = 0, p_z of a row, Eq. (pz_gaussian):
+ * rate d rho, noise variance sigma_n^2; which = 1, p_e of a row pair,
+ * Eq. (pe_gaussian): rate 2 d rho, noise variance 2 sigma_n^2.  The decoder,
+ * log_posterior and tail_constants all build them here.                     */
+static int orc_posterior_series(orc_series *S, int which, int d, double rho, double sigma_s, double sigma_n,
+                                int ell, int exact, double tol)
+{
+    double s2 = sigma_s * sigma_s, n2 = sigma_n * sigma_n;
+    double lam = (which == 0) ? d * rho : 2.0 * d * rho;
+    double vn = (which == 0) ? n2 : 2.0 * n2;
+    return orc_series_init(S, lam, s2, vn, ell, exact, tol);
+}
+
 /* log of the normalised posterior of Eq. (breve): log(p(w) / max_s p(s)).
  * Noiseless (v_noise = 0) reading: p is the indicator of w = 0, taken with
  * the tolerance tol, so log p_breve is 0 or -inf.                           */
@@ -445,15 +458,14 @@ static void orc_resolve(const orc_params *in, int d, int64_t n, int64_t m, int64
 
 static int orc_post_init(orc_post *P, int d, double rho, const orc_params *p)
 {
-    double s2 = p->sigma_s * p->sigma_s, n2 = p->sigma_n * p->sigma_n;
     P->drho = d * rho;
     if (p->learned) {
         if (!p->mlp || !(p->sigma_n > 0.0)) return ORC_EINVAL;
         for (int q = 0; q < ORC_MLP_PARAMS; ++q) P->mlp[q] = orc_bf16_to_double(p->mlp[q]);
     }
-    int rc = orc_series_init(&P->pz, d * rho, s2, n2, p->ell, 0, p->noiseless_tol);
+    int rc = orc_posterior_series(&P->pz, 0, d, rho, p->sigma_s, p->sigma_n, p->ell, 0, p->noiseless_tol);
     if (rc) return rc;
-    return orc_series_init(&P->pe, 2.0 * d * rho, s2, 2.0 * n2, p->ell, 0, p->noiseless_tol);
+    return orc_posterior_series(&P->pe, 1, d, rho, p->sigma_s, p->sigma_n, p->ell, 0, p->noiseless_tol);
 }
 
 /* Table "scores".  All three take the decision in exact-math form:
@@ -839,10 +851,7 @@ int orc_log_posterior(int which, int mode, int d, double rho, double sigma_s, do
                       int ell, double tol, int64_t count, const double *w, double *out, double *raw_out)
 {
     orc_series S;
-    double s2 = sigma_s * sigma_s, n2 = sigma_n * sigma_n;
-    double lam = (which == 0) ? d * rho : 2.0 * d * rho;
-    double vn = (which == 0) ? n2 : 2.0 * n2;
-    int rc = orc_series_init(&S, lam, s2, vn, ell, mode == 1, tol);
+    int rc = orc_posterior_series(&S, which, d, rho, sigma_s, sigma_n, ell, mode == 1, tol);
     if (rc) return rc;
     for (int64_t i = 0; i < count; ++i) {
         out[i] = orc_log_pbreve(&S, w[i]);
@@ -856,10 +865,7 @@ int orc_tail_constants(int which, int d, double rho, double sigma_s, double sigm
                        double *R, double *v_tail)
 {
     orc_series S;
-    double s2 = sigma_s * sigma_s, n2 = sigma_n * sigma_n;
-    double lam = (which == 0) ? d * rho : 2.0 * d * rho;
-    double vn = (which == 0) ? n2 : 2.0 * n2;
-    int rc = orc_series_init(&S, lam, s2, vn, ell, 0, 1e-5);
+    int rc = orc_posterior_series(&S, which, d, rho, sigma_s, sigma_n, ell, 0, 1e-5);
     if (rc) return rc;
     *R = S.R;
     *v_tail = S.v_tail;

@@ -1,0 +1,73 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in a copy of
+oracle/rl0_oracle.c (a dropped or doubled term, a wrong index, a reversed test, a
+swapped operand), builds the copy, and runs the oracle pin files against it through
+RL0_ORACLE_LIB: at least one pin must fail, other than the literal restatement of a
+round.  The unmutated copy must pass, so that a
+broken harness cannot pass for a caught mistake."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "rl0_oracle.c")
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_adaptive.py"]
+# the literal Python restatement of a round is left out: a catch must come from
+# a pin that does not retype the oracle's formulas
+LITERAL = "tests/test_oracle_pins.py::test_one_round_matches_a_literal_python_round"
+
+MUTANTS = [
+    ("posterior variance counts the noise twice (Eq. pz_gaussian)",
+     "S->v[q] = q * s2 + v_noise;", "S->v[q] = q * s2 + 2.0 * v_noise;"),
+    ("tail variance with R(ell) in place of R(ell-1)",
+     "S->v_tail = (s2 * lam * R_lm1 + v_noise * R_l) / R_l;", "S->v_tail = (s2 * lam * R_l + v_noise * R_l) / R_l;"),
+    ("Poisson tail recurrence off by one",
+     "term *= lam / (q + 1);", "term *= lam / (q + 2);"),
+    ("p_e without the doubled noise variance (Eq. pe_gaussian)",
+     "double vn = (which == 0) ? n2 : 2.0 * n2;", "double vn = (which == 0) ? n2 : n2;"),
+    ("p_e with rate d rho in place of 2 d rho",
+     "double lam = (which == 0) ? d * rho : 2.0 * d * rho;", "double lam = (which == 0) ? d * rho : d * rho;"),
+    ("p_z and p_e swapped in the decoder",
+     "int rc = orc_posterior_series(&P->pz, 0,", "int rc = orc_posterior_series(&P->pz, 1,"),
+    ("n_z sums 1 - q_z",
+     "nz += orc_qz(P, p->quantised, rl[l], t);", "nz += 1.0 - orc_qz(P, p->quantised, rl[l], t);"),
+    ("anchor test against log t in place of log(1 - t)",
+     "double lim = (t >= 1.0) ? -INFINITY : log(1.0 - t);\n    if (t <= 0.0) return 1;",
+     "double lim = (t <= 0.0) ? -INFINITY : log(t);\n    if (t <= 0.0) return 1;"),
+    ("consensus value from the anchor's residual",
+     "num += rl[l] * q;", "num += ri * q;"),
+    ("l1 test reversed",
+     "} else if (lhs <= rhs && score >= p->alpha) {", "} else if (lhs >= rhs && score >= p->alpha) {"),
+    ("the update overwrites x_j instead of adding omega",
+     "if (best >= 0) { xp[j] = xh[j] + best_w; upd++; }", "if (best >= 0) { xp[j] = best_w; upd++; }"),
+    ("H_k breaks ties towards the larger index",
+     "return (u->j > v->j) - (u->j < v->j);", "return (u->j < v->j) - (u->j > v->j);"),
+    ("residual with the sign reversed",
+     "rp[i] = yhat[i] - rp[i];", "rp[i] = rp[i] - yhat[i];"),
+]
+
+
+def _run_pins(tmp_path, text):
+    c = tmp_path / "orc.c"
+    c.write_text(text)
+    so = tmp_path / "liborc.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(c), "-lm"])
+    env = dict(os.environ, RL0_ORACLE_LIB=str(so))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS,
+                           "--deselect", LITERAL],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+
+
+def test_the_unmutated_copy_passes_the_pins(tmp_path):
+    r = _run_pins(tmp_path, open(SRC).read())
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    r = _run_pins(tmp_path, src.replace(old, new))
+    # exit code 1: collected and ran, and a pin failed (not a collection or usage error)
+    assert r.returncode == 1 and " failed" in r.stdout, (name, r.returncode, r.stdout[-2000:])

@@ -399,3 +399,28 @@ def test_one_round_corrects_shifted_entries_back_to_the_truth(quantised):
     np.testing.assert_allclose(xp[sh], I.x[sh], atol=6 * sn)
     others = np.setdiff1d(np.arange(n), sh)
     assert np.count_nonzero(xp[others] != xh[others]) <= 2
+
+
+@pytest.mark.parametrize("quantised", [False, True])
+def test_the_consensus_averages_the_rows_noise(quantised):
+    # An isolated support column shifted by s_j has rows -s_j + eta_i, i in N(j).  The
+    # update's value is a posterior-weighted mean of those rows (Table "scores"), so
+    # x'_j - x_j carries an average of about d noise terms: rms near sigma / sqrt(d),
+    # where any single row's value would leave rms sigma.
+    n, m, k, d, sn = 20000, 5000, 150, 7, 1e-2
+    I, y = _instance(dict(n=n, m=m, k=k, d=d, sigma_n=sn), 31, f32=False)
+    A = _A(I.rows, m)
+    rng = np.random.default_rng(4)
+    supp = I.support
+    cnt = np.bincount(I.rows[supp].ravel(), minlength=m)
+    iso = np.array([j for j in supp if np.all(cnt[I.rows[j]] == 1)])
+    assert iso.size >= 25
+    xh = I.x.astype(np.float64).copy()
+    xh[iso] += rng.choice([-1, 1], iso.size) * rng.uniform(0.3, 1.0, iso.size)
+    c = oracle.default_c(quantised, m / n, k / m)
+    xp, _, _, _ = oracle.round_step(I.rows, y, k, int(round(0.5 / c)), xh, y - A @ xh, sigma_n=sn,
+                                    quantised=quantised)
+    moved = iso[xp[iso] != xh[iso]]
+    assert moved.size >= 0.8 * iso.size
+    rms = math.sqrt(np.mean((xp[moved] - I.x[moved]) ** 2))
+    assert rms < 0.7 * sn, rms / sn
