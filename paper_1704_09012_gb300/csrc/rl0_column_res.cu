@@ -141,8 +141,9 @@ __device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsu
 
 // One round's column score up to the CTA's commit (load, stream, resolve).
 // DMAX slots per column; EXACT: d == DMAX (the slot guards fold away).
+// cur, round: the decode state's accepted buffer and round (read by the caller).
 template <int DMAX, bool IND, bool EXACT, int NT>
-__device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm)
+__device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm, int cur, int round)
 {
     // exact d <= 8: two columns per thread in FP16 lanes (code_candidates2)
     constexpr bool PAIRED = EXACT && DMAX <= 8;
@@ -153,9 +154,8 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm)
     const unsigned short *s_code = (const unsigned short *)dsm;
     const float *s_pz = (const float *)(dsm + a.res_pz_off);
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
-    const int cur = st->cur;
     const float2 *__restrict__ rz = cur ? a.rz1 : a.rz0;
-    const RoundThr th = a.thr[st->round];
+    const RoundThr th = a.thr[round];
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&S.bar);
     if (tid == 0) {
         S.count = 0;
@@ -443,8 +443,10 @@ template <int DMAX, bool IND, bool EXACT, int NT>
 __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    if (a.st->done) return;
-    column_phase<DMAX, IND, EXACT, NT>(a, dsm);
+    // done, cur and round in one L2 trip (the code copy waits on cur)
+    const int done = a.st->done, cur = a.st->cur, round = a.st->round;
+    if (done) return;
+    column_phase<DMAX, IND, EXACT, NT>(a, dsm, cur, round);
     // the codes are no longer needed: their bytes become H_k's scratch
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
     HkShared &hk = *(HkShared *)dsm;

@@ -355,9 +355,11 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
 __global__ void __launch_bounds__(256) k_scatter(KArgs a)
 {
     DecodeState *st = a.st;
-    if (st->done || st->upd_count == 0) return;
-    scatter_items(a, st->list_count, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                  (long long)gridDim.x * blockDim.x);
+    // the state words the loop needs, in one L2 trip
+    const int done = st->done;
+    const unsigned upd = st->upd_count, total = st->list_count;
+    if (done || upd == 0) return;
+    scatter_items(a, total, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 
