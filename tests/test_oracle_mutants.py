@@ -45,6 +45,17 @@ MUTANTS = [
      "return (u->j > v->j) - (u->j < v->j);", "return (u->j < v->j) - (u->j > v->j);"),
     ("residual with the sign reversed",
      "rp[i] = yhat[i] - rp[i];", "rp[i] = rp[i] - yhat[i];"),
+    ("stop level m sigma sqrt(1/pi) in place of m sigma sqrt(2/pi)",
+     "return (double)m * p->sigma_n * sqrt(2.0 / ORC_PI);", "return (double)m * p->sigma_n * sqrt(1.0 / ORC_PI);"),
+    ("adaptive_k floor at m/10",
+     "double floor_k = floor((double)m / 100.0);", "double floor_k = floor((double)m / 10.0);"),
+    ("adaptive_k sums p_z in place of 1 - p_z",
+     "if (xhat[j] != 0.0) s += 1.0 - exp(orc_log_pbreve(&P->pz, xhat[j]));",
+     "if (xhat[j] != 0.0) s += exp(orc_log_pbreve(&P->pz, xhat[j]));"),
+    ("one round too few in the sweep",
+     "return (int)ceil(1.0 / c - 1e-9);", "return (int)ceil(1.0 / c - 1e-9) - 1;"),
+    ("expander columns may repeat a row",
+     "if (!dup) col[got++] = cand;", "col[got++] = cand;"),
 ]
 
 

@@ -215,6 +215,18 @@ def _instance(cfg, seed, f32=True):
     return I, y
 
 
+def test_stop_level_is_the_noise_l1_the_model_leaves():
+    # Section "Stopping conditions": a decode stops once ||r_hat||_1 is at the level the
+    # noise alone leaves, E||eta||_1; against the mean of ||eta||_1 over noise draws of
+    # the generator (not the moment formula), within 1% (the mean's std is about 0.2%).
+    cfg = gm.config_small()
+    I, y = _instance(cfg, 0)
+    _, st, _ = oracle.decode(I.rows, y, I.k, sigma_n=I.sigma_n)
+    l1 = np.mean([np.abs(gm.draw_noise(I.m, I.sigma_n, 5000 + s).astype(np.float64)).sum() for s in range(400)])
+    assert st["stop_level"] == pytest.approx(l1, rel=0.01)
+    assert st["converged"] == int(st["final_l1"] <= st["stop_level"])
+
+
 def test_round_at_t_equal_one_updates_nothing_with_noise():
     # reading: 1 - p_z(r) >= 1 needs p_z(r) = 0, which never holds for sigma_n > 0
     I, y = _instance(gm.config_small(), 0)
