@@ -143,12 +143,36 @@ class ClockSampler:
 COLUMN_KERNEL_SOURCES = ["rl0_column_res.cu", "rl0_round.cuh", "rl0_device.cuh", "rl0_common.cuh"]
 
 
+def _code_only(src):
+    """C/C++ source without its comments, trailing blanks and empty lines (string and
+    character literals kept), so that counters stay tied to the code they measured."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     for f in COLUMN_KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc", f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "rl0.h"), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_1704_09012_gb300", "csrc", f)).read()).encode())
+    h.update(_code_only(open(os.path.join(ROOT, "include", "rl0.h")).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -478,8 +478,8 @@ __device__ __forceinline__ CodeThr code_thresholds(float ta, float tz, float rea
 //    of rows with |v| <= tz_in);
 //  - n_e at most 1 + the number of rows that can be near (q_e <= 1).
 // Returns a superset of the anchors that pass Alg. 2's test on the FP32
-// residuals (the resolve then applies anchor_candidates' tighter bound to the
-// few survivors: here, per column, it would cost more than it saves).
+// residuals; the resolve keeps those that are anchors on the FP32 residuals
+// and tests them exactly.
 template <int DMAX, bool IND>
 __device__ __forceinline__ unsigned code_candidates(const unsigned short *codes, const float *pzlb, const int *rid,
                                                     int d, const CodeThr &ct, float need)
