@@ -1,7 +1,7 @@
 """Pins of the learned-scorer parts of the oracle: the FP64 network and its gradient
-(finite differences), the C and NumPy forwards against each other, the feature vector on a
-hand-worked example, and the learned rule reducing to Algorithm 2's rule for weights that
-compute logit = 100 (n_e - n_z)/d - 50."""
+(finite differences), the C and NumPy forwards against each other, a hand-built network
+whose function is known, the feature vector on a hand-worked example, and the learned rule
+reducing to Algorithm 2's rule for weights that compute logit = 100 (n_e - n_z)/d - 50."""
 import math
 
 import numpy as np
@@ -39,6 +39,27 @@ def test_c_and_numpy_forward_agree():
     w, F, _ = _rand(2, 200)
     o, _ = mlp.forward(w, F)
     np.testing.assert_allclose(oracle.mlp_logits(w, F), o, rtol=1e-12, atol=1e-12)
+
+
+def test_a_hand_built_network_computes_its_function():
+    # Layer 1 copies f0 and f1 through its ReLU, layer 2 forms relu(h0 - h1) and
+    # relu(h1 - h0), the output adds them: logit = |relu(f0) - relu(f1)|.  A ReLU left
+    # out or a weight matrix read transposed changes the value (without the second
+    # layer's ReLU the two halves cancel); the other 14 features have zero weight.
+    P = {name: np.zeros(size) for name, size in mlp.SIZES}
+    W1 = P["W1"].reshape(mlp.NF, mlp.H)
+    W2 = P["W2"].reshape(mlp.H, mlp.H)
+    W1[0, 0] = W1[1, 1] = 1.0
+    W2[0, 0] = W2[1, 1] = 1.0
+    W2[1, 0] = W2[0, 1] = -1.0
+    P["w3"][:2] = 1.0
+    w = np.concatenate([P[name].ravel() for name, _ in mlp.SIZES])
+    rng = np.random.default_rng(7)
+    F = np.abs(rng.standard_normal((6, 16))) + 0.5
+    F[:, :2] = [[0.7, 0.2], [0.2, 0.7], [-0.7, 0.2], [0.3, -0.9], [-0.5, -0.1], [1.25, 1.25]]
+    want = np.abs(np.maximum(F[:, 0], 0.0) - np.maximum(F[:, 1], 0.0))
+    np.testing.assert_allclose(oracle.mlp_logits(w, F), want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(mlp.forward(w, F)[0], want, rtol=0, atol=1e-15)
 
 
 def test_features_on_a_worked_example():

@@ -1,8 +1,8 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake in a copy of
 oracle/rl0_oracle.c (a dropped or doubled term, a wrong index, a reversed test, a
 swapped operand), builds the copy, and runs the oracle pin files against it through
-RL0_ORACLE_LIB: at least one pin must fail, other than the literal restatement of a
-round.  The unmutated copy must pass, so that a
+RL0_ORACLE_LIB: at least one pin must fail, other than the restatements (the literal
+Python round, the NumPy copy of the network).  The unmutated copy must pass, so that a
 broken harness cannot pass for a caught mistake."""
 import os
 import subprocess
@@ -12,10 +12,11 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "rl0_oracle.c")
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_adaptive.py"]
-# the literal Python restatement of a round is left out: a catch must come from
-# a pin that does not retype the oracle's formulas
-LITERAL = "tests/test_oracle_pins.py::test_one_round_matches_a_literal_python_round"
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_adaptive.py", "tests/test_oracle_mlp.py"]
+# restatements are left out (the literal Python round, the NumPy copy of the
+# network): a catch must come from a pin that does not retype the oracle
+RESTATEMENTS = ["tests/test_oracle_pins.py::test_one_round_matches_a_literal_python_round",
+                "tests/test_oracle_mlp.py::test_c_and_numpy_forward_agree"]
 
 MUTANTS = [
     ("posterior variance counts the noise twice (Eq. pz_gaussian)",
@@ -56,6 +57,13 @@ MUTANTS = [
      "return (int)ceil(1.0 / c - 1e-9);", "return (int)ceil(1.0 / c - 1e-9) - 1;"),
     ("expander columns may repeat a row",
      "if (!dup) col[got++] = cand;", "col[got++] = cand;"),
+    ("learned scorer: second hidden layer without its ReLU",
+     "out += (a > 0.0 ? a : 0.0) * w3[o];", "out += a * w3[o];"),
+    ("learned scorer: first weight matrix read transposed",
+     "for (int i = 0; i < ORC_NFEAT; ++i) a += f[i] * W1[i * ORC_HID + o];",
+     "for (int i = 0; i < ORC_NFEAT; ++i) a += f[i] * W1[o * ORC_NFEAT + i];"),
+    ("learned scorer: n_e and n_z features swapped",
+     "f[7] = ne / d;\n    f[8] = nz / d;", "f[7] = nz / d;\n    f[8] = ne / d;"),
 ]
 
 
@@ -65,8 +73,8 @@ def _run_pins(tmp_path, text):
     so = tmp_path / "liborc.so"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(c), "-lm"])
     env = dict(os.environ, RL0_ORACLE_LIB=str(so))
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS,
-                           "--deselect", LITERAL],
+    deselect = [a for r in RESTATEMENTS for a in ("--deselect", r)]
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS, *deselect],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
