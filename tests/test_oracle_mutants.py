@@ -7,6 +7,7 @@ broken harness cannot pass for a caught mistake."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -78,15 +79,28 @@ def _run_pins(tmp_path, text):
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
-def test_the_unmutated_copy_passes_the_pins(tmp_path):
-    r = _run_pins(tmp_path, open(SRC).read())
+@pytest.fixture(scope="module")
+def runs(tmp_path_factory):
+    """Every copy (the unmutated one under the key None) built and run at once, one
+    process per copy, as many at a time as there are cores."""
+    src = open(SRC).read()
+    jobs = {None: src}
+    for name, old, new in MUTANTS:
+        assert src.count(old) == 1, name
+        jobs[name] = src.replace(old, new)
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        futs = {k: ex.submit(_run_pins, tmp_path_factory.mktemp("orc"), t) for k, t in jobs.items()}
+        return {k: f.result() for k, f in futs.items()}
+
+
+def test_the_unmutated_copy_passes_the_pins(runs):
+    r = runs[None]
     assert r.returncode == 0, r.stdout[-2000:]
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
-    src = open(SRC).read()
-    assert src.count(old) == 1, name
-    r = _run_pins(tmp_path, src.replace(old, new))
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_a_planted_mistake_fails_a_pin(runs, name):
+    r = runs[name]
     # exit code 1: collected and ran, and a pin failed (not a collection or usage error)
     assert r.returncode == 1 and " failed" in r.stdout, (name, r.returncode, r.stdout[-2000:])
