@@ -58,6 +58,8 @@ MUTANTS = [
      "return (int)ceil(1.0 / c - 1e-9);", "return (int)ceil(1.0 / c - 1e-9) - 1;"),
     ("expander columns may repeat a row",
      "if (!dup) col[got++] = cand;", "col[got++] = cand;"),
+    ("quantised q_z test reversed",
+     "return (lp >= lim) ? 1.0 : 0.0;", "return (lp <= lim) ? 1.0 : 0.0;"),
     ("learned scorer: second hidden layer without its ReLU",
      "out += (a > 0.0 ? a : 0.0) * w3[o];", "out += a * w3[o];"),
     ("learned scorer: first weight matrix read transposed",
