@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -93,7 +94,8 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (RL0_CLOCKS_CSV, else a temporary file); the JSON line carries their summary
+        self.path = os.environ.get("RL0_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), "rl0_clocks_bench.csv")
 
     def __enter__(self):
         try:
