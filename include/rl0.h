@@ -203,28 +203,41 @@ int rl0_decode_batched(int count, const rl0_expander *const *A, const float *con
  * counterpart: this is a deployment variant of Algorithm 2's loop.)
  *
  * Who needs it: code that must not call cudaMalloc or any other allocator
- * while it runs -- e.g. work issued while a stream is being captured into a
- * CUDA graph (an allocation there can synchronise the device and break the
- * capture), real-time loops whose memory budget is fixed at start-up, or
- * hosts whose own allocator already owns all free device memory.
+ * while it runs -- a real-time loop whose memory budget is fixed at
+ * start-up, or a host application whose own allocator already owns all free
+ * device memory, where a new allocation fails or evicts someone else's data.
  * rl0_decode does not allocate per call either, but its first call for a
  * given round count builds and instantiates a graph, which allocates.
  *
  * This entry point allocates nothing: its scratch is one file-scope device
  * array of about 3.6 MB compiled into the library, held by every GPU that
  * loads the library until the process exits.  The caller passes y_dev and
- * xhat_dev as for rl0_decode and gets the same result; the kernels are
- * launched directly on the stream.  Limits: n <= 65536, m <= 32768 (larger
- * instances return RL0_ERR_TOO_LARGE); adaptive_k returns RL0_ERR_UNSUPPORTED;
- * stats.ms and the profile fields stay 0.
+ * xhat_dev as for rl0_decode and gets the same result (with scorer = 1 that
+ * includes the analytic continuation described below); the kernels are
+ * launched directly on the stream, and the stream is synchronised before the
+ * call returns.  Limits: n <= 65536, m <= 32768 (larger instances return
+ * RL0_ERR_TOO_LARGE); adaptive_k returns RL0_ERR_UNSUPPORTED; stats.ms and
+ * the profile fields stay 0; the decode keeps no round log (rl0_decode_log
+ * then reports 0 rounds).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same array and clears the
- * parts that must start at zero; calls that overlap on the GPU (from other
- * streams or host threads) race on it, so serialise them. */
+ * (cudaGetSymbolAddress) with that device current.  Every call reuses the
+ * same array and clears the parts that must start at zero.  Calls that
+ * overlap on the GPU (from other streams or host threads) race on the array,
+ * and calls on one expander also share its pinned host staging block with
+ * rl0_decode and rl0_round_step: serialise them. */
 int rl0_decode_static(const rl0_expander *A, const float *y_dev, int64_t k,
                       const rl0_params *params, float *xhat_dev, rl0_stats *stats,
                       void *cuda_stream);
+
+/* Failure-detection test hook.  The column kernel waits for the bulk copy of
+ * the residual codes into shared memory with a bounded poll loop (2^22 polls
+ * of mbarrier.try_wait).  polls >= 0 makes that first wait on this expander
+ * give up after `polls` polls (0: at once); the kernel then records
+ * RL0_ERR_TIMEOUT, waits for its copies in flight with the built-in limit,
+ * scores nothing and returns, and rl0_decode returns RL0_ERR_TIMEOUT with the
+ * device still usable.  polls < 0 restores the built-in limit.  Affects
+ * rl0_decode calls made after it on this expander. */
+int rl0_expander_set_wait_polls(rl0_expander *A, int64_t polls);
 
 /* Per-round record of the last rl0_decode on this expander (host copy kept by
  * the library).  Writes min(cap, rounds) records and returns the number of

@@ -21,7 +21,8 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
+_use_openmp = False
 
 
 class Params(C.Structure):
@@ -75,12 +76,28 @@ COLREC_DTYPE = np.dtype([
     ("score", np.float64), ("nz", np.float64), ("min_margin", np.float64)], align=True)
 
 
+class openmp:
+    """Within this context the oracle calls go to its OpenMP build (the column loop of a
+    round shared among the host's cores; same results as the serial build).  Used for
+    full-size checks and the multi-core CPU baseline."""
+
+    def __enter__(self):
+        global _use_openmp
+        self._prev = _use_openmp
+        _use_openmp = True
+        return self
+
+    def __exit__(self, *a):
+        global _use_openmp
+        _use_openmp = self._prev
+
+
 def lib():
-    global _lib
-    if _lib is None:
+    key = bool(_use_openmp) and not os.environ.get("RL0_ORACLE_LIB")
+    if key not in _libs:
         # RL0_ORACLE_LIB: a copy of the oracle built elsewhere (the planted-mistake
         # test runs the pins against mutated copies)
-        path = os.environ.get("RL0_ORACLE_LIB") or _build.build()
+        path = os.environ.get("RL0_ORACLE_LIB") or _build.build(openmp=key)
         L = C.CDLL(path)
         dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
         ip = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
@@ -113,8 +130,8 @@ def lib():
         assert L.orc_sizeof(1) == C.sizeof(Stats)
         assert L.orc_sizeof(2) == C.sizeof(RoundLog)
         assert L.orc_sizeof(3) == COLREC_DTYPE.itemsize
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 def _check(rc):

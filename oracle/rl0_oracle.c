@@ -561,10 +561,18 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                    double *xp, double *rp, int64_t *updated, orc_col_rec *rec)
 {
     int64_t upd = 0;
-    double *rl = (double *)malloc((size_t)d * sizeof(double));
-    if (!rl) return ORC_ENOMEM;
+    int nomem = 0;
     for (int64_t j = 0; j < n; ++j) xp[j] = xh[j];
+    /* Every column reads only rh and writes only xp[j] and rec[j], so the
+     * columns may be scored in any order: the OpenMP build of this file
+     * shares them among threads and gives the serial build's results. */
+#pragma omp parallel reduction(+ : upd, nomem)
+    {
+    double *rl = (double *)malloc((size_t)d * sizeof(double));
+    if (!rl) nomem = 1;
+#pragma omp for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
+        if (!rl) continue;
         const int32_t *N = rows + j * d;
         for (int l = 0; l < d; ++l) rl[l] = rh[N[l]];
         double nz = 0.0;
@@ -638,6 +646,8 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
         }
     }
     free(rl);
+    }
+    if (nomem) return ORC_ENOMEM;
     int rc = orc_hard_threshold(n, k, xp);
     if (rc) return rc;
     /* r <- y - A x'  (Alg. 2 uses the measured y-hat as y; reading) */

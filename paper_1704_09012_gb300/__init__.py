@@ -30,7 +30,8 @@ ERRORS = {
 EXPORTS = [
     "rl0_make_expander", "rl0_expander_from_rows", "rl0_expander_rows", "rl0_expander_shape",
     "rl0_free_expander", "rl0_sketch", "rl0_decode", "rl0_decode_host", "rl0_round_step",
-    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static", "rl0_parallel_l0",
+    "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static", "rl0_expander_set_wait_polls",
+    "rl0_parallel_l0",
     "rl0_posterior_mc",
     "rl0_candidate_features", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
     "rl0_mlp_forward", "rl0_mlp_params",
@@ -100,6 +101,7 @@ def _lib():
                                          C.POINTER(vp), vp, vp]
         L.rl0_decode_log.argtypes = [vp, C.POINTER(RoundRecord), i32]
         L.rl0_decode_static.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.POINTER(Stats), vp]
+        L.rl0_expander_set_wait_polls.argtypes = [vp, i64]
         L.rl0_parallel_l0.argtypes = [vp, vp, C.c_double, C.c_double, i32, vp, C.POINTER(Stats), vp]
         L.rl0_posterior_mc.argtypes = [vp, vp, vp, i64, C.c_double, C.c_double, i32, C.c_double, C.c_double,
                                        vp, vp, vp]
@@ -213,9 +215,10 @@ def decode(A, y, k, out=None, stream=None, **params):
 
 def decode_static(A, y, k, out=None, stream=None, **params):
     """rl0_decode without any allocation (fixed workspace inside the library; n <= 65536,
-    m <= 32768).  For callers that cannot allocate device memory while they run, e.g.
-    during stream capture or under a memory budget fixed at start-up; `out` lets them
-    pass a preallocated x_hat as well.  Calls share the workspace: do not overlap them."""
+    m <= 32768).  For callers that cannot allocate device memory while they run (a memory
+    budget fixed at start-up, or an allocator of their own that owns the free memory);
+    `out` lets them pass a preallocated x_hat as well.  Calls share the workspace: do not
+    overlap them."""
     p = make_params(**params)
     x = out if out is not None else torch.empty(A.n, dtype=torch.float32, device="cuda")
     st = Stats()
@@ -223,6 +226,13 @@ def decode_static(A, y, k, out=None, stream=None, **params):
                                     _dev(x, torch.float32, A.n, "x_hat"), C.byref(st), _stream(stream)),
            "rl0_decode_static")
     return x, st.as_dict()
+
+
+def set_wait_polls(A, polls):
+    """Failure-detection test hook (rl0_expander_set_wait_polls): polls >= 0 makes the column
+    kernel's first bounded wait on A give up after that many polls (0: at once), so the next
+    decode returns RL0_ERR_TIMEOUT; polls < 0 restores the built-in limit."""
+    _check(_lib().rl0_expander_set_wait_polls(A.handle, int(polls)), "rl0_expander_set_wait_polls")
 
 
 def parallel_l0(A, y, alpha=0.0, tol=0.0, max_iter=0, out=None, stream=None):

@@ -80,9 +80,9 @@ unsigned res_region_bytes(long long m, int nt, size_t scratch)
     return (unsigned)((std::max(std::max(codes, hk), scratch) + 15) & ~(size_t)15);
 }
 
-__device__ __forceinline__ bool mbar_try_wait_bounded(unsigned bar, unsigned parity)
+__device__ __forceinline__ bool mbar_try_wait_bounded(unsigned bar, unsigned parity, unsigned polls)
 {
-    for (unsigned it = 0; it < RL0_RES_WAIT_LIMIT; ++it) {
+    for (unsigned it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -196,14 +196,18 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm,
         nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
         if constexpr (PAIRED) nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
     }
+    // polls of the first wait: the built-in limit, or the expander's test
+    // setting (rl0_expander_set_wait_polls), which may make it give up at once
+    const unsigned polls = ctx->wait_test ? ctx->wait_polls : RL0_RES_WAIT_LIMIT;
     __syncthreads();                               // the barrier is initialised
-    const bool arrived = mbar_try_wait_bounded(bar, 0u);
+    const bool arrived = mbar_try_wait_bounded(bar, 0u, polls);
     if (__syncthreads_or(!arrived || __ldcg(&st->status) == (int)RL0_ERR_CUDA)) {
-        // a copy did not complete in time: record it, give the copies one more
-        // bounded wait, skip the columns (the last-CTA count below still runs)
+        // a copy did not complete in time: record it, wait for the copies in
+        // flight once more (with the built-in limit) before this CTA's shared
+        // memory is reused, skip the columns (the last-CTA count below still runs)
         if (tid == 0 && !arrived) {
             atomicCAS(&st->status, 0, (int)RL0_ERR_TIMEOUT);
-            mbar_try_wait_bounded(bar, 0u);
+            mbar_try_wait_bounded(bar, 0u, RL0_RES_WAIT_LIMIT);
         }
         j0 = hi;
     }

@@ -119,6 +119,8 @@ struct DecodeCtx {
     int always_accept;        // Alg. 1 (Parallel-l0): keep every iteration, stop when one changes nothing
     int skip_t1;              // sigma_n > 0: the round at t = 1 provably changes nothing; record it only
     float conv_tol;           // Alg. 1: converged when every |r_i| <= conv_tol (0: Alg. 2's stop level)
+    int wait_test;            // 0: the column kernel's first bounded wait makes its built-in number
+    unsigned wait_polls;      // of polls; 1: it makes wait_polls (rl0_expander_set_wait_polls)
 };
 
 struct UndoEntry {
@@ -164,6 +166,8 @@ struct rl0_expander {
     int last_log_rounds;      // rounds recorded by the last rl0_decode
     void *events;             // CUDA events used to time decodes
     void *table_cache;        // host tables of the last parameter set
+    int wait_test;            // rl0_expander_set_wait_polls: override the first bounded wait
+    unsigned wait_polls;
 };
 
 #define RL0_MAX_ROUNDS 1024

@@ -895,6 +895,46 @@ static int get_graph(rl0_expander *A, int nrounds, int dmax, int indicator, int 
     return RL0_OK;
 }
 
+// Alg. 2 with the analytic scores, continued from the x_hat a learned decode
+// left (a fresh sweep): the analytic tables, the state rebuilt from x_hat, then
+// every round of the sweep launched directly, and the final residual norm.
+// `a` holds the buffers the kernels use (an expander's workspace or the static
+// array).  When the kernels bound n_z with the residual codes (a.pzlb set),
+// the analytic scores' p_z bound table is uploaded too: the learned decode
+// does not upload one, and a table left by an earlier decode with other
+// parameters would drop valid candidates.  *launches receives the kernels
+// launched.  Enqueues only; the caller synchronises.
+static int launch_analytic_continuation(rl0_expander *A, const KArgs &a, int64_t k, const Resolved &R,
+                                        const float *y_dev, float *xhat_dev, int *launches, cudaStream_t s)
+{
+    HostStage *H = (HostStage *)A->host_pinned;
+    Resolved R2 = R;
+    R2.p.scorer = 0;
+    R2.p.profile = 0;
+    rl0::fill_tables(A->m, A->d, k, R2, &H->ctx, H->thr, R2.nrounds);
+    H->ctx.y = y_dev;
+    H->ctx.x = xhat_dev;
+    H->ctx.want_log = 0;
+    H->ctx.passed = nullptr;
+    CK(cudaMemcpyAsync(a.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)a.thr, H->thr, R2.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
+    if (a.pzlb && !R2.indicator) {
+        rl0::pz_lower_bounds(A->m, A->d, k, R2, H->pzlb);
+        CK(cudaMemcpyAsync((void *)a.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(a.st, 0, sizeof(DecodeState), s));
+    const int dmax = dmax_of(A->d);
+    k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
+    k_rows_from_x<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+    k_start<<<1, 32, 0, s>>>(a, 0, 0);
+    k_list_count_from_support<<<1, 32, 0, s>>>(a);
+    for (int r = 0; r < R2.nrounds; ++r) launch_round(a, dmax, R2.indicator, 0, s);
+    k_final_sum<<<1, 32, 0, s>>>(a);
+    CK(cudaGetLastError());
+    *launches = 4 + 3 * R2.nrounds + 1;
+    return RL0_OK;
+}
+
 // Alg. 2 with the adaptive_k flag: the rounds of the captured graph, launched
 // one round at a time; after each accepted round the host reads the support,
 // takes the adaptive_k step in FP64 (ascending column order) and uploads the
@@ -960,6 +1000,8 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
         H->ctx.want_log = 1;
         H->ctx.passed = nullptr;
         H->ctx.stop_level = stop_level;
+        H->ctx.wait_test = A->wait_test;
+        H->ctx.wait_polls = A->wait_polls;
         CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
         if (!R.indicator) {
@@ -1012,6 +1054,8 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     H->ctx.x = xhat_dev;
     H->ctx.want_log = 1;
     H->ctx.passed = nullptr;
+    H->ctx.wait_test = A->wait_test;
+    H->ctx.wait_polls = A->wait_polls;
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
@@ -1074,27 +1118,10 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         // (||r||_1 > E||eta||_1 + 3 sqrt(Var||eta||_1)): Algorithm 2 with the
         // analytic scores continues from the learned x_hat (a fresh sweep).
         const DecodeState first = H->st;
-        Resolved R2 = R;
-        R2.p.scorer = 0;
-        R2.p.profile = 0;
-        rl0::fill_tables(A->m, A->d, k, R2, &H->ctx, H->thr, R2.nrounds);
-        H->ctx.y = y_dev;
-        H->ctx.x = xhat_dev;
-        H->ctx.want_log = 0;
-        H->ctx.passed = nullptr;
-        CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(w.thr, H->thr, R2.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
-        CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
         const KArgs a = make_args(A);
-        k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
-        k_rows_from_x<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
-        k_start<<<1, 32, 0, s>>>(a, 0, 0);
-        k_list_count_from_support<<<1, 32, 0, s>>>(a);
-        for (int r = 0; r < R2.nrounds; ++r) {
-            launch_round(a, dmax, R2.indicator, 0, s);
-        }
-        k_final_sum<<<1, 32, 0, s>>>(a);
-        CK(cudaGetLastError());
+        int cont_launches = 0;
+        rc = launch_analytic_continuation(A, a, k, R, y_dev, xhat_dev, &cont_launches, s);
+        if (rc) return rc;
         if (stats) CK(cudaEventRecord(ev[1], s));
         CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1112,7 +1139,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
             stats->fallback_rounds = first.fallback_rounds + H->st.fallback_rounds;
             stats->analytic_rounds = H->st.rounds_run;
             stats->skipped_rounds = first.skipped + H->st.skipped;
-            stats->launches += 4 + 3 * R2.nrounds + 1;
+            stats->launches += cont_launches;
         }
     }
     return RL0_OK;
@@ -1134,6 +1161,14 @@ extern "C" int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int 
         out[r].k_prior = H->kprior[r];
     }
     return A->last_log_rounds;
+}
+
+extern "C" int rl0_expander_set_wait_polls(rl0_expander *A, int64_t polls)
+{
+    if (!A || polls > (int64_t)0xffffffffu) return RL0_ERR_INVALID_ARG;
+    A->wait_test = polls >= 0 ? 1 : 0;
+    A->wait_polls = polls >= 0 ? (unsigned)polls : 0u;
+    return RL0_OK;
 }
 
 extern "C" int rl0_decode(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
@@ -1441,22 +1476,39 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&H->st, base + L.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    A->last_log_rounds = 0;                       // this decode keeps no round log
     if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
+    const DecodeState first = H->st;
+    int launches = launches_unrolled(R.nrounds) + 1;          // and k_final_sum
+    int cont = 0;
+    if (!first.status && R.p.scorer == 1 && !(first.l1_hat <= R.keep_level)) {
+        // as rl0_decode: the learned result's residual is not noise-like, so
+        // Alg. 2 with the analytic scores continues from its x_hat (the L2
+        // column kernel here: the static array holds no residual codes)
+        int nl = 0;
+        rc = launch_analytic_continuation(A, a, k, R, y_dev, xhat_dev, &nl, s);
+        if (rc) return rc;
+        launches += nl;
+        CK(cudaMemcpyAsync(&H->st, base + L.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        cont = 1;
+    }
     if (stats) {
-        const double l1 = H->st.final_l1;
         std::memset(stats, 0, sizeof(*stats));
-        stats->rounds = H->st.rounds_run;
-        stats->accepted_rounds = H->st.accepted_rounds;
+        stats->rounds = (cont ? first.rounds_run : 0) + H->st.rounds_run;
+        stats->accepted_rounds = (cont ? first.accepted_rounds : 0) + H->st.accepted_rounds;
         stats->converged = H->st.converged;
         stats->status = H->st.status;
         stats->support_size = H->st.nnz;
-        stats->final_l1 = l1;
-        stats->hk_rounds = H->st.hk_rounds;
-        stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = launches_unrolled(R.nrounds) + 1;      // and k_final_sum
-        stats->skipped_rounds = H->st.skipped;
+        stats->final_l1 = H->st.final_l1;
+        stats->hk_rounds = (cont ? first.hk_rounds : 0) + H->st.hk_rounds;
+        stats->fallback_rounds = (cont ? first.fallback_rounds : 0) + H->st.fallback_rounds;
+        stats->launches = launches;
+        stats->analytic_rounds = cont ? H->st.rounds_run : 0;
+        stats->skipped_rounds = (cont ? first.skipped : 0) + H->st.skipped;
     }
-    return H->st.status ? RL0_ERR_TIMEOUT : RL0_OK;
+    if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
+    return RL0_OK;
 }
 
 extern "C" int rl0_candidate_features(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,

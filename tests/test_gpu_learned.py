@@ -237,3 +237,51 @@ def test_trained_scorer_against_the_analytic_rule(rl0, trained):
     assert res[:, 1].mean() >= res[:, 0].mean()           # no loss of recovery
     for p_ in par:
         assert p_[0] and p_[1] <= 1e-5
+
+
+def test_learned_continuation_bounds_with_its_own_posteriors(rl0):
+    """The analytic continuation of a learned decode bounds n_z with the p_z table of its own
+    parameters, whatever an earlier decode on the same expander left behind.  Here an
+    analytic decode at 20x the noise level runs first (a broader p_z, so larger n_z bounds);
+    the learned decode that follows accepts nothing, so its continuation is Alg. 2 from
+    x_hat = 0 and must equal the oracle's learned decode with the same network."""
+    I, y32 = _problem(4096, 1024, 100, 7, 1e-3, 3)
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
+    y = torch.from_numpy(y32).cuda()
+    rl0.decode(A, y, I.k, sigma_n=20 * I.sigma_n)
+    bits = np.zeros(rl0.MLP_PARAMS, np.uint16)
+    bits[-1] = 0xBF80                                     # logit -1 for every input: accept nothing
+    wb = torch.from_numpy(bits.view(np.int16)).cuda()
+    xl, sl = rl0.decode(A, y, I.k, sigma_n=I.sigma_n, scorer=1, mlp=wb)
+    assert sl["analytic_rounds"] > 0 and sl["accepted_rounds"] > 0
+    xo, so, _ = oracle.decode(I.rows, y32.astype(np.float64), I.k, sigma_n=I.sigma_n, mlp_bf16=bits)
+    assert so["analytic_rounds"] > 0
+    xg = xl.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
+    assert sl["accepted_rounds"] == so["accepted_rounds"]
+
+
+def test_learned_decode_at_scale_matches_oracle(rl0, trained):
+    """The learned decode at the learned workload's evaluation shape (delta = 0.1,
+    rho = 0.15, SNR 30 dB, d = 7) at n = 2^20 -- the oracle's learned decode at n = 2^22
+    takes too long for a test -- against the oracle's learned decode with the same BF16
+    network, analytic continuation included."""
+    n, d = 1 << 20, 7
+    m = int(0.1 * n)
+    k = int(0.15 * m)
+    sn = gm.sigma_from_snr(d, k / m, 30.0)
+    I, y32 = _problem(n, m, k, d, sn, 4242)
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), m)
+    xl, sl = rl0.decode(A, torch.from_numpy(y32).cuda(), k, sigma_n=sn, scorer=1, mlp=trained["wb"])
+    with oracle.openmp():
+        xo, so, _ = oracle.decode(I.rows, y32.astype(np.float64), k, sigma_n=sn, mlp_bf16=trained["bits"])
+    xg = xl.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print("\nlearned n=2^20: rounds %d/%d (continuation %d/%d) accepted %d/%d rel_l2 %.2e" % (
+        sl["rounds"], so["rounds"], sl["analytic_rounds"], so["analytic_rounds"], sl["accepted_rounds"],
+        so["accepted_rounds"], rel))
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert rel <= 1e-5
+    assert sl["rounds"] == so["rounds"] and sl["analytic_rounds"] == so["analytic_rounds"]
+    assert sl["accepted_rounds"] == so["accepted_rounds"]

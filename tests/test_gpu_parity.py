@@ -119,9 +119,15 @@ def _states(I, y64, rng):
 
 
 def _compare_round(rl0, A, I, y32, rows, k, ridx, x32, r32, quantised):
+    """One round from (x32, r32) on both sides.  Decisions whose oracle margin is below
+    MARGIN may differ; every other decision must agree, and x' and r are compared element
+    by element everywhere a differing decision cannot reach: the columns that differ, the
+    entries H_k kept on one side only (a differing decision can move H_k's cut), and the
+    rows of those columns are left out of the comparison, everything else is checked."""
     y64 = y32.astype(np.float64)
-    xo, ro, updo, rec = oracle.round_step(rows, y64, k, ridx, x32.astype(np.float64), r32.astype(np.float64),
-                                          sigma_n=I.sigma_n, quantised=quantised)
+    with oracle.openmp():
+        xo, ro, updo, rec = oracle.round_step(rows, y64, k, ridx, x32.astype(np.float64), r32.astype(np.float64),
+                                              sigma_n=I.sigma_n, quantised=quantised)
     xg, rg, passed, l1g = rl0.round_step(A, _cuda(y32), k, ridx, _cuda(x32), _cuda(r32), sigma_n=I.sigma_n,
                                          quantised=quantised)
     xg = xg.cpu().numpy().astype(np.float64)
@@ -129,14 +135,25 @@ def _compare_round(rl0, A, I, y32, rows, k, ridx, x32, r32, quantised):
     pg = passed.cpu().numpy().astype(bool)
     po = rec["passed"].astype(bool)
     near = rec["min_margin"] < MARGIN
-    assert np.array_equal(pg[~near], po[~near]), np.nonzero(pg != po)[0][:10]
-    if np.array_equal(pg, po):
-        assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
-        assert _rel(xg, xo) <= XTOL
-        Aabs = _A(rows, I.m)
-        # FP32 row sum (a few terms) plus what the FP32 consensus values in x' carry over
-        scale = np.abs(y64) + Aabs @ np.abs(xo)
-        assert np.all(np.abs(rg - ro) <= 4 * scale * 2 ** -24 + Aabs @ np.abs(xg - xo) + 1e-30)
+    flip = np.nonzero(pg != po)[0]
+    assert near[flip].all(), flip[~near[flip]][:10]
+    # entries whose H_k outcome differs beyond the flipped columns themselves
+    hk_only = np.setdiff1d(np.nonzero((xg != 0) != (xo != 0))[0], flip)
+    assert hk_only.size <= 2 * flip.size, (flip.size, hk_only.size)
+    out = np.union1d(flip, hk_only)
+    keep = np.ones(I.n, bool)
+    keep[out] = False
+    assert np.array_equal(xg[keep] != 0, xo[keep] != 0)
+    assert _rel(xg[keep], xo[keep]) <= XTOL
+    Aabs = _A(rows, I.m)
+    rows_out = np.zeros(I.m, bool)
+    if out.size:
+        rows_out[np.unique(rows[out].ravel())] = True
+    # FP32 row sum (a few terms) plus what the FP32 consensus values in x' carry over
+    scale = np.abs(y64) + Aabs @ np.abs(xo)
+    ok_r = np.abs(rg - ro) <= 4 * scale * 2 ** -24 + Aabs @ np.abs(np.where(keep, xg - xo, 0.0)) + 1e-30
+    assert np.all(ok_r[~rows_out])
+    if flip.size == 0:
         assert l1g == pytest.approx(np.abs(ro).sum(), rel=1e-6)
     return int(near.sum()), int(po.sum()), int(near.size)
 
@@ -288,6 +305,8 @@ def test_full_size_round_and_decode_properties(rl0):
     for q in (False, True):
         c = oracle.default_c(q, I.m / I.n, I.k / I.m)
         nr, npass, ncols = _compare_round(rl0, A, I, y32, I.rows, I.k, int(0.5 / c), x32, r32, q)
+        print("\nn=2^20 round (%s): %d passing columns, %d decisions within the margin %.0e"
+              % ("quantised" if q else "continuous", npass, nr, MARGIN))
         assert npass > 1000 and nr <= 2 + ncols // 1000
     # the whole decode in the benchmark's configuration: invariants at full size
     xg, st = rl0.decode(A, _cuda(y32), I.k, sigma_n=I.sigma_n)
