@@ -210,7 +210,7 @@ int rl0_decode_batched(int count, const rl0_expander *const *A, const float *con
  * given round count builds and instantiates a graph, which allocates.
  *
  * This entry point allocates nothing: its scratch is one file-scope device
- * array of about 3.6 MB compiled into the library, held by every GPU that
+ * array of about 6 MB compiled into the library, held by every GPU that
  * loads the library until the process exits.  The caller passes y_dev and
  * xhat_dev as for rl0_decode and gets the same result (with scorer = 1 that
  * includes the analytic continuation described below); the kernels are

@@ -24,7 +24,8 @@
 //            evaluated one per thread, then one thread per candidate (column,
 //            slot) sums them, and each column takes its highest passing slot
 //            (the last passing anchor in row order); the CTA then commits with
-//            one global atomic per counter;
+//            one global atomic per counter, and the columns that became
+//            nonzero go into the rebuild's fresh row buckets;
 //   H_k      the launch's last CTA (an acquire-release ticket) applies H_k
 //            when |supp x'| > k, its scratch in the bytes that held the codes.
 // The resolve runs the arithmetic of k_column_score in the same order, so
@@ -143,7 +144,7 @@ __device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsu
 // DMAX slots per column; EXACT: d == DMAX (the slot guards fold away).
 // cur, round: the decode state's accepted buffer and round (read by the caller).
 template <int DMAX, bool IND, bool EXACT, int NT>
-__device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm, int cur, int round)
+__device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
 {
     // exact d <= 8: two columns per thread in FP16 lanes (code_candidates2)
     constexpr bool PAIRED = EXACT && DMAX <= 8;
@@ -154,6 +155,24 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm,
     const unsigned short *s_code = (const unsigned short *)dsm;
     const float *s_pz = (const float *)(dsm + a.res_pz_off);
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
+    // this CTA's columns: [lo, hi), equal shares of n
+    const int lo = (int)(((long long)blockIdx.x * n) / gridDim.x);
+    const int hi = (int)(((long long)(blockIdx.x + 1) * n) / gridDim.x);
+    int j0 = lo;
+    // row ids of this thread's first column(s): j0 + tid (and j0 + NT + tid
+    // when paired), loaded while the previous kernel finishes (A never changes)
+    int nxt[DMAX], nxb[PAIRED ? DMAX : 1];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        const int j = j0 + tid;
+        nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+        if constexpr (PAIRED) nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
+    }
+    pdl_wait();                                    // the previous rebuild's r, codes, x and state
+    // done, cur and round in one L2 trip (the code copy waits on cur)
+    const int done = st->done, cur = st->cur, round = st->round;
+    pdl_launch_dependents();
+    if (done) return false;
     const float2 *__restrict__ rz = cur ? a.rz1 : a.rz0;
     const RoundThr th = a.thr[round];
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&S.bar);
@@ -182,19 +201,6 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm,
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                              :: "r"(dst + a.res_pz_off), "l"(a.pzlb), "r"(4u * RL0_PZ_BINS), "r"(bar) : "memory");
         }
-    }
-    // this CTA's columns: [lo, hi), equal shares of n
-    const int lo = (int)(((long long)blockIdx.x * n) / gridDim.x);
-    const int hi = (int)(((long long)(blockIdx.x + 1) * n) / gridDim.x);
-    int j0 = lo;
-    // row ids of this thread's first column(s): j0 + tid (and j0 + NT + tid
-    // when paired)
-    int nxt[DMAX], nxb[PAIRED ? DMAX : 1];
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-        const int j = j0 + tid;
-        nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
-        if constexpr (PAIRED) nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
     }
     // polls of the first wait: the built-in limit, or the expander's test
     // setting (rl0_expander_set_wait_polls), which may make it give up at once
@@ -428,8 +434,9 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm,
             const int nup = (int)(tpf & 0xffffu);
             if (nup != ngone) atomicAdd(&st->nnz_delta, nup - ngone);
             if (ngone) atomicAdd(&st->zeroed, (unsigned)ngone);
-            S.ubase = (tpf >> 16) ? atomicAdd(&st->upd_count, tpf >> 16) : 0u;
-            S.fbase = (tpf & 0xffffu) ? atomicAdd(&st->list_count, tpf & 0xffffu) : 0u;
+            const unsigned long long old2 = (tpf != 0u) ? take_upd_list(st, tpf >> 16, tpf & 0xffffu) : 0ull;
+            S.ubase = (unsigned)(old2 >> 32);
+            S.fbase = (unsigned)old2;
         }
         __syncthreads();
         if (pass) {
@@ -438,19 +445,23 @@ __device__ __forceinline__ void column_phase(const KArgs &a, unsigned char *dsm,
             u.old = old;
             a.ulog[S.ubase + (pf >> 16)] = u;
         }
-        if (fresh) a.list[S.fbase + (pf & 0xffffu)] = j;
+        if (fresh) {
+            a.list[S.fbase + (pf & 0xffffu)] = j;
+            int rid[DMAX];
+#pragma unroll
+            for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? __ldg(a.rows_sm + (size_t)s2 * n + j) : 0;
+            bucket_column<DMAX>(a, j, rid, d);
+        }
         __syncthreads();                           // the scratch is reused by the next batch
     }
+    return true;
 }
 
 template <int DMAX, bool IND, bool EXACT, int NT>
 __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    // done, cur and round in one L2 trip (the code copy waits on cur)
-    const int done = a.st->done, cur = a.st->cur, round = a.st->round;
-    if (done) return;
-    column_phase<DMAX, IND, EXACT, NT>(a, dsm, cur, round);
+    if (!column_phase<DMAX, IND, EXACT, NT>(a, dsm)) return;     // the decode is done
     // the codes are no longer needed: their bytes become H_k's scratch
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
     HkShared &hk = *(HkShared *)dsm;
@@ -546,8 +557,8 @@ bool rl0_res_launch(const KArgs &a, int indicator, cudaStream_t s)
     if (!a.res_ok) return false;
 #define RL0_CR(D, E) do {                                                                                   \
         constexpr int NT_ = ResNT<D, E>::value;                                                              \
-        if (indicator) k_column_score_res<D, true, E, NT_><<<a.res_grid, NT_, a.res_smem, s>>>(a);         \
-        else k_column_score_res<D, false, E, NT_><<<a.res_grid, NT_, a.res_smem, s>>>(a);                  \
+        if (indicator) launch_pdl(k_column_score_res<D, true, E, NT_>, a.res_grid, NT_, a.res_smem, s, a); \
+        else launch_pdl(k_column_score_res<D, false, E, NT_>, a.res_grid, NT_, a.res_smem, s, a);          \
     } while (0)
     switch (res_variant(a.d)) {
     case 6: RL0_CR(6, true); break;

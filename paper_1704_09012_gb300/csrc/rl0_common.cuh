@@ -67,11 +67,13 @@ struct DecodeState {
     int status;
     int round;
     int cur;                  // which rz buffer holds r_hat
-    unsigned shat_count;      // |supp x_hat|: list[0 .. shat_count) is the support
     unsigned list_count;      // support + columns that became nonzero this round
-    unsigned upd_count;       // updates this round (undo log length)
+    unsigned upd_count;       // updates this round (undo log length); with list_count one 8-byte
+                              // word, so that a CTA takes slots in both with one atomic
+    unsigned shat_count;      // |supp x_hat|: list[0 .. shat_count) is the support
     unsigned drop_count;      // entries H_k zeroed this round (undo log length)
-    int overflow;             // a row had more than RL0_BUCKET contributors
+    int overflow;             // a row's fresh bucket received more than RL0_BUCKET columns
+    unsigned bflags;          // bit b: support bucket B[b] incomplete (a row with > RL0_BUCKET columns)
     int converged;            // ||r_hat||_1 <= stop level
     unsigned nnz;             // |supp x_hat|
     int nnz_delta;            // change of the nonzero count made by this round's updates
@@ -138,8 +140,10 @@ struct Workspace {
     int *list_tmp;            // compaction scratch, capacity n
     UndoEntry *ulog;          // updates of this round, capacity n
     UndoEntry *dlog;          // H_k drops of this round, capacity n
-    int *bcnt;                // per-row contributor counts, int[m] (kept zero between rounds)
-    int *bkt;                 // per-row contributor columns, int[m * RL0_BUCKET]
+    int *bcnt;                // per-row fresh-bucket counts, int[m] (kept zero between rounds)
+    int *bkt;                 // per-row fresh-bucket columns, int[m * RL0_BUCKET]
+    int *sbcnt[2];            // per-row support-bucket counts B[0], B[1], int[m] each
+    int *sbkt[2];             // per-row support-bucket columns, int[m * RL0_BUCKET] each
     double *l1part;           // per-chunk l1 partials
     unsigned long long *hk_scratch;  // H_k candidate keys, capacity n
     DecodeState *st;

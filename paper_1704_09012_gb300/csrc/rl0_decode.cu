@@ -3,7 +3,7 @@
 // coefficients (host, FP64), the round kernels, and the captured CUDA graph
 // that replays the loop.
 //
-// One round, as three kernels on one stream:
+// One round, as two or three kernels on one stream:
 //   column score  every column j bounds, then scores, its anchors (Table
 //                 "scores", Eqs. (ne_nz_1), (ne_nz_2)), applies the last
 //                 passing update to x in place and logs it for undo
@@ -11,7 +11,8 @@
 //                 shared memory; k_column_score below: L2 gathers).  The
 //                 launch's last CTA applies H_k (radix select on the 63-bit
 //                 key (|x_j| bits, ~j): ties go to the smaller j);
-//   scatter       the support's (row, column) pairs into per-row buckets;
+//   scatter       the support's (row, column) pairs into per-row buckets
+//                 (the resident-code column kernel does this itself);
 //   rebuild       r_i = y_i - sum of x_j over row i in ascending j, FP32 (and
 //                 the same sum in FP32 pairs, about 48 bits, for the final
 //                 residual check), with p_z(r_i), the residual code, and l1
@@ -56,6 +57,11 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from(KArgs a, const flo
     DF l1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
     if (i < a.m) {
+        // a decode starts with empty row buckets (x_hat = 0, or an injected
+        // x_hat whose support k_bucket_support adds next)
+        a.sbcnt0[i] = 0;
+        a.sbcnt1[i] = 0;
+        a.bcnt[i] = 0;
         const float r = src[i];
         if (!isfinite(r)) atomicExch(&a.st->status, (int)RL0_ERR_INVALID_Y);
         const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, r);
@@ -340,6 +346,8 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
     constexpr int NT = ColBlock<DMAX>::value;
     __shared__ ColShared<DMAX, NT, LEARNED> S;
     const DecodeState *st = a.st;
+    pdl_wait();                                    // the previous rebuild's r, x and state
+    pdl_launch_dependents();
     if (st->done) return;
     const DecodeCtx *ctx = a.ctx;
     const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
@@ -352,14 +360,12 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_column_score(KArgs a)
 // ---------------------------------------------------------------------------
 // Residual rebuild r = y - A x'.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scatter(KArgs a)
+// An injected x_hat's support (list[0, shat_count)) into the support bucket
+// B[0] (emptied by k_rows_from / k_rows_from_x).
+__global__ void __launch_bounds__(256) k_bucket_support(KArgs a)
 {
-    DecodeState *st = a.st;
-    // the state words the loop needs, in one L2 trip
-    const int done = st->done;
-    const unsigned upd = st->upd_count, total = st->list_count;
-    if (done || upd == 0) return;
-    scatter_items(a, total, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    bucket_support_items(a, a.st->shat_count, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                         (long long)gridDim.x * blockDim.x);
 }
 
 
@@ -371,20 +377,27 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     DecodeState *st = a.st;
     const DecodeCtx *ctx = a.ctx;
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
-    // the row's inputs do not depend on the state: they load beside it
+    // y_i and the support buckets load while the column kernel finishes; the
+    // fresh bucket and the state words after it has
     RowIn pre;
-    if (i < a.m) pre = load_row_inputs(a, ctx, i);
-    if (st->done) return;
+    if (i < a.m) load_row_support(a, ctx, i, pre);
+    pdl_wait();
+    if (i < a.m) load_row_fresh(a, i, pre);
+    const int done = st->done, cur = st->cur, ovf = st->overflow;
+    const unsigned upd = st->upd_count, bfl = st->bflags;
+    pdl_launch_dependents();
+    if (done) return;
     const int no_accept = ctx->no_accept;
-    const unsigned upd = st->upd_count;
     if (upd == 0) {                                // nothing changed: r = r_hat, only t advances
         if (blockIdx.x == 0 && !no_accept) accept_step<RL0_ROWS_CHUNK>(a, 0u, s_scan);
         return;
     }
-    const bool csr = st->overflow != 0;        // a bucket overflowed: full CSR(A^T) pass
-    const int cur = st->cur;
+    // a full fresh bucket, or an incomplete support bucket: CSR(A^T) pass
+    const bool csr = ovf != 0 || ((bfl >> cur) & 1u);
     DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
-    if (i < a.m) rebuild_row(a, ctx, i, csr, cur, l1, f1, &pre);
+    bool fits = true;
+    if (i < a.m) fits = rebuild_row(a, ctx, i, csr, cur, l1, f1, pre);
+    if (__syncthreads_or(!fits) && threadIdx.x == 0) atomicOr(&st->bflags, 1u << (cur ^ 1));
     // ||r||_1 of the FP32 residual, and ||y_hat - A x'||_1 without FP32 rounding
     const double2 s2 = block_sum2_df(l1, f1, sha, shb);
     if (threadIdx.x == 0) {
@@ -428,6 +441,9 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
     DF l1{0.0f, 0.0f}, f1{0.0f, 0.0f};
     const int i = blockIdx.x * RL0_ROWS_CHUNK + threadIdx.x;
     if (i < a.m) {
+        a.sbcnt0[i] = 0;                           // k_bucket_support fills B[0] next
+        a.sbcnt1[i] = 0;
+        a.bcnt[i] = 0;
         float sum = 0.0f;
         DF acc{ctx->y[i], 0.0f};
         for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
@@ -545,16 +561,19 @@ struct GraphEntry {
 // 6- and 39-round decodes (2 and 4 were slower).
 #define RL0_ROUNDS_PER_ITER 3
 
-// Kernels one decode graph launches: prologue (2), 3 per round in whole loop
+// Kernels of one round: the column score and the rebuild.
+int kernels_per_round(const KArgs &, int) { return 2; }
+
+// Kernels one decode graph launches: prologue (2), kpr per round in whole loop
 // iterations (the step that ends the decode takes the final residual norm).
-int launches_per_decode(int nrounds)
+int launches_per_decode(int nrounds, int kpr)
 {
     const int iters = (nrounds + RL0_ROUNDS_PER_ITER - 1) / RL0_ROUNDS_PER_ITER;
-    return 2 + 3 * RL0_ROUNDS_PER_ITER * iters;
+    return 2 + kpr * RL0_ROUNDS_PER_ITER * iters;
 }
 
 // The same with every round launched on its own (profile graph).
-int launches_unrolled(int nrounds) { return 2 + 3 * nrounds; }
+int launches_unrolled(int nrounds, int kpr) { return 2 + kpr * nrounds; }
 
 struct GraphCache {
     std::vector<GraphEntry> entries;
@@ -587,6 +606,10 @@ KArgs make_args(const rl0_expander *A)
     a.dlog = w.dlog;
     a.bcnt = w.bcnt;
     a.bkt = w.bkt;
+    a.sbcnt0 = w.sbcnt[0];
+    a.sbcnt1 = w.sbcnt[1];
+    a.sbkt0 = w.sbkt[0];
+    a.sbkt1 = w.sbkt[1];
     a.l1part = w.l1part;
     a.hkkey = w.hk_scratch;
     a.st = w.st;
@@ -599,10 +622,12 @@ KArgs make_args(const rl0_expander *A)
     return a;
 }
 
-void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
+// Launches the column score (+ H_k in its last CTA).  Returns true when it is
+// the resident-code kernel, which also fills the rebuild's buckets.
+bool launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-    if (!learned && rl0_res_launch(a, indicator, s)) return;
-#define RL0_CS(D, I, L) k_column_score<D, I, L><<<rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s>>>(a)
+    if (!learned && rl0_res_launch(a, indicator, s)) return true;
+#define RL0_CS(D, I, L) launch_pdl(k_column_score<D, I, L>, rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s, a)
     if (learned) {
         if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }
         else { if (indicator) RL0_CS(16, true, true); else RL0_CS(16, false, true); }
@@ -610,16 +635,28 @@ void launch_column_score(const KArgs &a, int dmax, int indicator, int learned, c
     else if (dmax == 16) { if (indicator) RL0_CS(16, true, false); else RL0_CS(16, false, false); }
     else { if (indicator) RL0_CS(32, true, false); else RL0_CS(32, false, false); }
 #undef RL0_CS
+    return false;
 }
 
 int dmax_of(int d) { return d <= 8 ? 8 : (d <= 16 ? 16 : 32); }
+
+// The residual rebuild of a round (+ accept in the rebuild's last CTA).
+void launch_rebuild(const KArgs &a, cudaStream_t s)
+{
+    launch_pdl(k_rebuild, a.nchunks, RL0_ROWS_CHUNK, 0, s, a);
+}
 
 // The kernels of one round (shared by the graph and by round_step).
 void launch_round(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
     launch_column_score(a, dmax, indicator, learned, s);   // + H_k in its last CTA
-    k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
-    k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);     // + accept in its last CTA
+    launch_rebuild(a, s);
+}
+
+// An injected x_hat's support into the support bucket B[0].
+void launch_bucket_support(const KArgs &a, cudaStream_t s)
+{
+    k_bucket_support<<<2 * a.nsm, 256, 0, s>>>(a);
 }
 
 // The round loop as a graph.  Normal decodes: prologue kernels, then a WHILE
@@ -710,8 +747,7 @@ int capture_decode_graph(rl0_expander *A, int nrounds, int dmax, int indicator, 
         launch_column_score(a, dmax, indicator, learned, s);
         if (e == cudaSuccess) e = mark(4 * r + 1);
         if (e == cudaSuccess) e = mark(4 * r + 2);
-        k_scatter<<<2 * a.nsm, 256, 0, s>>>(a);
-        k_rebuild<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
+        launch_rebuild(a, s);
         if (e == cudaSuccess) e = mark(4 * r + 3);
     }
     if (e == cudaSuccess) e = mark(4 * nrounds);
@@ -770,6 +806,10 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.dlog, n * sizeof(UndoEntry));
     al((void **)&w.bcnt, m * sizeof(int));
     al((void **)&w.bkt, m * RL0_BUCKET * sizeof(int));
+    al((void **)&w.sbcnt[0], m * sizeof(int));
+    al((void **)&w.sbcnt[1], m * sizeof(int));
+    al((void **)&w.sbkt[0], m * RL0_BUCKET * sizeof(int));
+    al((void **)&w.sbkt[1], m * RL0_BUCKET * sizeof(int));
     al((void **)&w.l1part, nchunks * sizeof(double));
     al((void **)&w.hk_scratch, n * sizeof(unsigned long long));
     al((void **)&w.st, sizeof(DecodeState));
@@ -778,6 +818,8 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.rlog, RL0_MAX_ROUNDS * sizeof(RoundLog));
     al((void **)&w.final_part, 2 * nchunks * sizeof(double));   // one set per rz buffer
     if (e == cudaSuccess) e = cudaMemset(w.bcnt, 0, m * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w.sbcnt[0], 0, m * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w.sbcnt[1], 0, m * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(w.st, 0, sizeof(DecodeState));
     if (e == cudaSuccess) e = cudaMallocHost(&A->host_pinned, sizeof(HostStage));
     if (e != cudaSuccess) { cudaGetLastError(); return rl0_cuda_err(e); }
@@ -823,8 +865,9 @@ void rl0_workspace_free(rl0_expander *A)
         delete (TableCache *)A->table_cache;
         A->table_cache = nullptr;
     }
-    void *ptrs[] = {w.rz[0], w.rz[1], w.code[0], w.code[1], w.pzlb, w.res_list, w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt, w.l1part,
-                    w.hk_scratch, w.st, w.ctx, w.thr, w.rlog, w.final_part};
+    void *ptrs[] = {w.rz[0], w.rz[1], w.code[0], w.code[1], w.pzlb, w.res_list, w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt,
+                    w.sbcnt[0], w.sbcnt[1], w.sbkt[0], w.sbkt[1], w.l1part, w.hk_scratch, w.st, w.ctx, w.thr, w.rlog,
+                    w.final_part};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&w, 0, sizeof(w));
 }
@@ -928,10 +971,11 @@ static int launch_analytic_continuation(rl0_expander *A, const KArgs &a, int64_t
     k_rows_from_x<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a);
     k_start<<<1, 32, 0, s>>>(a, 0, 0);
     k_list_count_from_support<<<1, 32, 0, s>>>(a);
+    launch_bucket_support(a, s);
     for (int r = 0; r < R2.nrounds; ++r) launch_round(a, dmax, R2.indicator, 0, s);
     k_final_sum<<<1, 32, 0, s>>>(a);
     CK(cudaGetLastError());
-    *launches = 4 + 3 * R2.nrounds + 1;
+    *launches = 5 + kernels_per_round(a, 0) * R2.nrounds + 1;
     return RL0_OK;
 }
 
@@ -966,7 +1010,7 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
     for (int r = H->st.round; r < R.nrounds && !H->st.done; ++r) {
         H->kprior[r] = kprior;
         launch_round(a, dmax, R.indicator, 0, s);
-        launches += 3;
+        launches += kernels_per_round(a, 0);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1093,7 +1137,9 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
         stats->ms = ms;
         stats->hk_rounds = H->st.hk_rounds;
         stats->fallback_rounds = H->st.fallback_rounds;
-        stats->launches = prof ? launches_unrolled(R.nrounds) : launches_per_decode(H->st.rounds_run - H->st.skipped);
+        const int kpr = kernels_per_round(make_args(A), learned);
+        stats->launches = prof ? launches_unrolled(R.nrounds, kpr)
+                               : launches_per_decode(H->st.rounds_run - H->st.skipped, kpr);
         stats->skipped_rounds = H->st.skipped;
         if (prof) {
             float acc[4] = {0, 0, 0, 0};
@@ -1274,7 +1320,7 @@ extern "C" int rl0_parallel_l0(const rl0_expander *Ac, const float *y_dev, doubl
         stats->support_size = H->st.nnz;
         stats->final_l1 = H->st.final_l1;
         stats->ms = ms;
-        stats->launches = launches_per_decode(H->st.rounds_run);
+        stats->launches = launches_per_decode(H->st.rounds_run, kernels_per_round(make_args(A), 0));
     }
     if (H->st.status) return H->st.status < 0 ? H->st.status : RL0_ERR_TIMEOUT;
     return RL0_OK;
@@ -1323,6 +1369,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     k_support_from_x<<<rl0_div_up(a.n, 256), 256, 0, s>>>(a);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
     k_list_count_from_support<<<1, 32, 0, s>>>(a);
+    launch_bucket_support(a, s);
     launch_round(a, dmax_of(A->d), R.indicator, R.p.scorer == 1, s);
     k_extract_r<<<2 * a.nsm, 256, 0, s>>>(a, rp_dev, 0);
     CK(cudaGetLastError());
@@ -1352,7 +1399,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
 // a call never asks the CUDA allocator (or any other allocator) for memory and
 // never builds a graph (instantiating one allocates).  The price: instances are
 // limited to n <= RL0_STATIC_MAX_N and m <= RL0_STATIC_MAX_M, every GPU that
-// loads the library keeps the array (about 3.6 MB) until the process exits,
+// loads the library keeps the array (about 6 MB) until the process exits,
 // and all calls share it, so calls that overlap on the GPU (other streams,
 // other host threads) race and must be serialised by the caller.
 // ---------------------------------------------------------------------------
@@ -1363,7 +1410,8 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
 
 // Byte layout of the static workspace (each piece 256-byte aligned).
 struct StaticLayout {
-    size_t rz0, rz1, list, ulog, dlog, bcnt, bkt, l1part, final_part, hkkey, st, ctx, thr, rlog, total;
+    size_t rz0, rz1, list, ulog, dlog, bcnt, bkt, sbcnt0, sbcnt1, sbkt0, sbkt1, l1part, final_part, hkkey, st, ctx, thr,
+        rlog, total;
 };
 
 static constexpr StaticLayout static_layout()
@@ -1377,6 +1425,10 @@ static constexpr StaticLayout static_layout()
     L.dlog = o; o += RL0_STATIC_ALIGN(sizeof(UndoEntry) * RL0_STATIC_MAX_N);
     L.bcnt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M);
     L.bkt = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M * RL0_BUCKET);
+    L.sbcnt0 = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M);
+    L.sbcnt1 = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M);
+    L.sbkt0 = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M * RL0_BUCKET);
+    L.sbkt1 = o; o += RL0_STATIC_ALIGN(sizeof(int) * RL0_STATIC_MAX_M * RL0_BUCKET);
     L.l1part = o; o += RL0_STATIC_ALIGN(sizeof(double) * RL0_STATIC_CHUNKS);
     L.final_part = o; o += RL0_STATIC_ALIGN(sizeof(double) * 2 * RL0_STATIC_CHUNKS);
     L.hkkey = o; o += RL0_STATIC_ALIGN(sizeof(unsigned long long) * RL0_STATIC_MAX_N);
@@ -1440,6 +1492,10 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     a.dlog = (UndoEntry *)(base + L.dlog);
     a.bcnt = (int *)(base + L.bcnt);
     a.bkt = (int *)(base + L.bkt);
+    a.sbcnt0 = (int *)(base + L.sbcnt0);
+    a.sbcnt1 = (int *)(base + L.sbcnt1);
+    a.sbkt0 = (int *)(base + L.sbkt0);
+    a.sbkt1 = (int *)(base + L.sbkt1);
     a.l1part = (double *)(base + L.l1part);
     a.final_part = (double *)(base + L.final_part);
     a.hkkey = (unsigned long long *)(base + L.hkkey);
@@ -1479,7 +1535,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     A->last_log_rounds = 0;                       // this decode keeps no round log
     if (H->st.status == RL0_ERR_INVALID_Y) return RL0_ERR_INVALID_Y;
     const DecodeState first = H->st;
-    int launches = launches_unrolled(R.nrounds) + 1;          // and k_final_sum
+    int launches = launches_unrolled(R.nrounds, kernels_per_round(a, R.p.scorer == 1)) + 1;   // and k_final_sum
     int cont = 0;
     if (!first.status && R.p.scorer == 1 && !(first.l1_hat <= R.keep_level)) {
         // as rl0_decode: the learned result's residual is not noise-like, so

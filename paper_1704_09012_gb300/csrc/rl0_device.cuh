@@ -214,6 +214,36 @@ __device__ __forceinline__ double warp_sum_parts_l2(const double *parts, int npa
     return v;
 }
 
+// The same sum (warp_sum_parts's order: lane l of warp 0 adds chunks l,
+// l + 32, ... in turn, then the xor butterfly) over partials written in this
+// launch, with all NT threads of the CTA first bringing 4 NT partials at a
+// time into shared memory sh (4 NT doubles): one L2 trip per 4 NT chunks
+// rather than one per four chunks of a lane.  Every thread of the CTA calls
+// it; the sum is valid in warp 0.
+template <int NT>
+__device__ __forceinline__ double cta_sum_parts_l2(const double *parts, int nparts, double *sh)
+{
+    static_assert((4 * NT) % 32 == 0, "blocks keep each chunk on its lane");
+    const int t = threadIdx.x;
+    double v = 0.0;
+    for (int c0 = 0; c0 < nparts; c0 += 4 * NT) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + q * NT + t;
+            if (c < nparts) sh[q * NT + t] = __ldcg(parts + c);
+        }
+        __syncthreads();
+        if (t < 32) {
+            const int lim = min(4 * NT, nparts - c0);
+            for (int c = t; c < lim; c += 32) v += sh[c];
+        }
+        __syncthreads();
+    }
+    if (t < 32)
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 // Sort 8 column ids ascending (Batcher's 19-comparator network).
 #define RL0_CSWAP(i, j) { const int lo_ = min(js[i], js[j]), hi_ = max(js[i], js[j]); js[i] = lo_; js[j] = hi_; }
 __device__ __forceinline__ void sort8(int *js)

@@ -6,6 +6,8 @@
 // the ABI.
 #pragma once
 
+#include <cstddef>
+
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
 
@@ -24,7 +26,8 @@ struct KArgs {
                                        // CTA b uses its column range
     int *list;
     UndoEntry *ulog, *dlog;
-    int *bcnt, *bkt;
+    int *bcnt, *bkt;                   // fresh buckets F (see the rebuild's row buckets below)
+    int *sbcnt0, *sbcnt1, *sbkt0, *sbkt1;   // support buckets B[0], B[1]
     double *l1part;
     unsigned long long *hkkey;
     DecodeState *st;
@@ -36,10 +39,70 @@ struct KArgs {
     int has_cond;
 };
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch between the round kernels.  A round kernel is
+// launched so that it may start while the kernel before it on the stream is
+// still running; before it touches anything that kernel writes it waits for
+// that kernel's completion (griddepcontrol.wait, which also makes its writes
+// visible), and only then lets the next kernel start early
+// (griddepcontrol.launch_dependents).  So a kernel overlaps only the tail of
+// its immediate predecessor, and what it reads before its wait (row ids, y,
+// the support buckets of the previous round) no kernel still running writes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch of kernel k on stream s with programmatic stream serialization
+// (errors are left for cudaGetLastError, as with <<< >>>).
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// Slots in the undo log (upd_count) and in the support list (list_count) for
+// nupd updates and nfresh new nonzeros, taken with one 64-bit atomic on the
+// two adjacent counters.  Returns the counters before: low word list_count,
+// high word upd_count (list_count stays below 2^32, so no carry crosses).
+__device__ __forceinline__ unsigned long long take_upd_list(DecodeState *st, unsigned nupd, unsigned nfresh)
+{
+    static_assert(offsetof(DecodeState, list_count) % 8 == 0 &&
+                  offsetof(DecodeState, upd_count) == offsetof(DecodeState, list_count) + 4, "counter pair layout");
+    return atomicAdd((unsigned long long *)&st->list_count, ((unsigned long long)nupd << 32) | nfresh);
+}
+
+// Column j, which became nonzero this round, into the fresh bucket of each of
+// its d rows (RL0_BUCKET per row; a fuller row sets the overflow flag, and
+// the rebuild then takes every row from CSR(A^T)).
+// The d <= DM atomics are issued before any store, so they overlap.
+template <int DM>
+__device__ __forceinline__ void bucket_column(const KArgs &a, int j, const int *rid, int d)
+{
+    int slot[DM];
+#pragma unroll
+    for (int s = 0; s < DM; ++s) slot[s] = (s < d) ? atomicAdd(&a.bcnt[rid[s]], 1) : 0;
+#pragma unroll
+    for (int s = 0; s < DM; ++s)
+        if (s < d) {
+            if (slot[s] < RL0_BUCKET) a.bkt[(long long)rid[s] * RL0_BUCKET + slot[s]] = j;
+            else a.st->overflow = 1;
+        }
+}
+
 // Column j's outcome: x_j += omega of its chosen anchor (best >= 0), with the
 // undo log, the support list and the nonzero count kept in step.  Every lane
 // of the warp calls it; the warp's leader takes its undo-log and list slots
-// with two independent atomics.
+// with one atomic (take_upd_list).
 __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *ctx, int j, bool active, int best,
                                               float bw)
 {
@@ -64,8 +127,9 @@ __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *c
         if (lane == leader) {
             if (dn) atomicAdd(&a.st->nnz_delta, dn);
             if (gone) atomicAdd(&a.st->zeroed, gone);
-            base = atomicAdd(&a.st->upd_count, (unsigned)__popc(mask));
-            if (fmask) fbase = atomicAdd(&a.st->list_count, (unsigned)__popc(fmask));
+            const unsigned long long old2 = take_upd_list(a.st, (unsigned)__popc(mask), (unsigned)__popc(fmask));
+            base = (unsigned)(old2 >> 32);
+            fbase = (unsigned)old2;
         }
         base = __shfl_sync(0xffffffffu, base, leader);
         fbase = __shfl_sync(0xffffffffu, fbase, leader);
@@ -76,7 +140,16 @@ __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *c
             e.old = old;
             a.ulog[base + __popc(mask & below)] = e;
         }
-        if (fresh) a.list[fbase + __popc(fmask & below)] = j;
+        if (fresh) {
+            a.list[fbase + __popc(fmask & below)] = j;
+            // into the rebuild's fresh buckets, up to 8 rows at a time
+            for (int s0 = 0; s0 < a.d; s0 += 8) {
+                int rid[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) rid[q] = (s0 + q < a.d) ? __ldg(a.rows_sm + (size_t)(s0 + q) * a.n + j) : 0;
+                bucket_column<8>(a, j, rid, min(8, a.d - s0));
+            }
+        }
     }
 }
 
@@ -112,138 +185,160 @@ __device__ __forceinline__ void last_cta_hk(const KArgs &a, const DecodeCtx *ctx
 }
 
 // ---------------------------------------------------------------------------
-// Scatter: the support's (row, column) pairs into per-row buckets, work items
-// w = e d + s (support entry e, slot s) from w0 in steps of ws.
+// The rebuild's row buckets.  Row i's contributors to r = y - A x' are kept in
+// two kinds of buckets of RL0_BUCKET column ids:
+//   support  B[b] (sbcnt_b, sbkt_b), b = 0, 1: the columns j of row i with
+//            x_hat_j != 0, for the x_hat whose residual is in rz[b] (so B[cur]
+//            describes r_hat); the rebuild writes B[cur ^ 1] for the candidate
+//            x', and accepting the round (cur ^= 1) makes it current;
+//   fresh    F (bcnt, bkt): columns that became nonzero this round, added by
+//            the column kernel as they commit; the rebuild empties it.
+// A support bucket that would need more than RL0_BUCKET entries sets bit b of
+// DecodeState::bflags (bucket b incomplete), a full fresh bucket sets
+// DecodeState::overflow, and either makes the rebuild take every row from
+// CSR(A^T).  Columns that H_k or an update set to zero stay in the buckets
+// until the next compaction and add an exact 0 to the sums.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void scatter_items(const KArgs &a, unsigned total, long long w0, long long ws)
+
+// x_hat's support (list[0, total)) into B[0], which must be empty: work items
+// w = e d + s (support entry e, slot s) from w0 in steps of ws.  Used where a
+// decode starts from an injected x_hat.
+__device__ __forceinline__ void bucket_support_items(const KArgs &a, unsigned total, long long w0, long long ws)
 {
-    const float *x = a.ctx->x;
     const int d = a.d;
     const long long work = (long long)total * d;
     for (long long w = w0; w < work; w += ws) {
         const unsigned e = (unsigned)(w / d);
         const int s = (int)(w % d);
         const int j = a.list[e];
-        // x_j and the row id in one L2 trip; entries that became zero add nothing
-        const float xj = x[j];
         const int row = a.rows_cm[(long long)j * d + s];
-        if (xj == 0.0f) continue;
-        const int slot = atomicAdd(&a.bcnt[row], 1);
-        if (slot < RL0_BUCKET) a.bkt[(long long)row * RL0_BUCKET + slot] = j;
-        else a.st->overflow = 1;
+        const int slot = atomicAdd(&a.sbcnt0[row], 1);
+        if (slot < RL0_BUCKET) a.sbkt0[(long long)row * RL0_BUCKET + slot] = j;
+        else atomicOr(&a.st->bflags, 1u);
     }
 }
 
-// A row's inputs to the rebuild that do not depend on the decode state: its
-// bucket count, the bucket's 8 slots and y_i (loaded side by side, one L2 trip).
+// A row's inputs to the rebuild: both support buckets, the fresh bucket and
+// y_i (both support buckets are loaded before the state says which one is
+// current, so that the loads do not wait on the state).
 struct RowIn {
-    int c;
-    int4 b0, b1;
+    int c0, c1, cf;
+    int4 b00, b01, b10, b11, f0, f1;
     float y;
 };
 
-__device__ __forceinline__ RowIn load_row_inputs(const KArgs &a, const DecodeCtx *ctx, int i)
+// The inputs no kernel of this round writes (y_i and both support buckets):
+// loaded before the rebuild waits for the column kernel.
+__device__ __forceinline__ void load_row_support(const KArgs &a, const DecodeCtx *ctx, int i, RowIn &in)
 {
-    RowIn in;
-    in.c = a.bcnt[i];
-    const int4 *bq = (const int4 *)(a.bkt + (long long)i * RL0_BUCKET);
-    in.b0 = bq[0];
-    in.b1 = bq[1];
+    in.c0 = a.sbcnt0[i];
+    in.c1 = a.sbcnt1[i];
+    const int4 *q0 = (const int4 *)(a.sbkt0 + (long long)i * RL0_BUCKET);
+    const int4 *q1 = (const int4 *)(a.sbkt1 + (long long)i * RL0_BUCKET);
+    in.b00 = q0[0];
+    in.b01 = q0[1];
+    in.b10 = q1[0];
+    in.b11 = q1[1];
     in.y = ctx->y[i];
-    return in;
 }
 
-// ---------------------------------------------------------------------------
-// Rebuild of R rows i[0..R) (has[r]: row r exists): r_i = y_i - sum of x_j
-// over the row in ascending j (FP32), the same sum in FP32 pairs for the final
-// residual check, p_z(r_i) and the residual code into the candidate buffer
-// (cur: the accepted one); l1 = |r_i|, f1 = |that pair sum|.  Every row's
-// loads are issued before any row's stores, so R rows cost one chain of L2
-// trips; pre, if not null, holds the rows' inputs already loaded.  csr: a
-// bucket overflowed, take the rows from CSR(A^T).
-// ---------------------------------------------------------------------------
-template <int R>
-__device__ __forceinline__ void rebuild_rows(const KArgs &a, const DecodeCtx *ctx, const int *i, const bool *has,
-                                             bool csr, int cur, DF *l1, DF *f1, const RowIn *pre = nullptr)
+// The fresh bucket, written by this round's column kernel.
+__device__ __forceinline__ void load_row_fresh(const KArgs &a, int i, RowIn &in)
 {
-    static_assert(RL0_BUCKET == 8, "sorting network is for 8 entries");
+    in.cf = a.bcnt[i];
+    const int4 *qf = (const int4 *)(a.bkt + (long long)i * RL0_BUCKET);
+    in.f0 = qf[0];
+    in.f1 = qf[1];
+}
+
+// Merge of two ascending runs js[0..8) and js[8..16) into one ascending run of
+// 16 (the second run reversed makes the sequence bitonic; then Batcher's
+// half-cleaners at strides 8, 4, 2, 1).
+#define RL0_CSWAP16(i, j) { const int lo_ = min(js[i], js[j]), hi_ = max(js[i], js[j]); js[i] = lo_; js[j] = hi_; }
+__device__ __forceinline__ void merge8x2(int *js)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { const int t = js[8 + q]; js[8 + q] = js[15 - q]; js[15 - q] = t; }
+#pragma unroll
+    for (int st = 8; st >= 1; st >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if ((q & st) == 0) RL0_CSWAP16(q, q + st)
+    }
+}
+#undef RL0_CSWAP16
+
+// ---------------------------------------------------------------------------
+// Row i of the candidate: r_i = y_i - sum of x'_j over the row in ascending j
+// (FP32), the same sum in FP32 pairs for the final residual check, p_z(r_i)
+// and the residual code into the candidate buffer (cur: the accepted one);
+// l1 = |r_i|, f1 = |that pair sum|.  The contributors are the support bucket
+// B[cur] and the fresh bucket merged into ascending order, or, when csr is
+// set, the row of CSR(A^T).  The row's entries with x'_j != 0 become the
+// candidate's support bucket B[cur ^ 1]; returns false when they do not fit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool rebuild_row(const KArgs &a, const DecodeCtx *ctx, int i, bool csr, int cur, DF &l1,
+                                            DF &f1, const RowIn &in)
+{
+    static_assert(RL0_BUCKET == 8, "sorting networks are for 8 entries");
     const float *x = ctx->x;
     float2 *rz = cur ? a.rz0 : a.rz1;              // the candidate buffer
-    float sum[R], yv[R];
-    DF acc[R];
+    int *ncnt = cur ? a.sbcnt0 : a.sbcnt1;         // the candidate's support bucket
+    int *nbkt = (cur ? a.sbkt0 : a.sbkt1) + (long long)i * RL0_BUCKET;
+    float sum = 0.0f;
+    DF acc{in.y, 0.0f};
+    int kept = 0;
     if (csr) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            sum[r] = 0.0f;
-            yv[r] = has[r] ? ctx->y[i[r]] : 0.0f;
-            acc[r] = DF{yv[r], 0.0f};
-            if (!has[r]) continue;
-            for (int p = a.rowptr[i[r]]; p < a.rowptr[i[r] + 1]; ++p) {
-                const float xv = x[a.colidx[p]];
-                sum[r] += xv;
-                acc[r] = df_sub(acc[r], xv);
+        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
+            const int j = a.colidx[p];
+            const float xv = x[j];
+            sum += xv;
+            acc = df_sub(acc, xv);
+            if (xv != 0.0f) {
+                if (kept < RL0_BUCKET) nbkt[kept] = j;
+                ++kept;
             }
-            a.bcnt[i[r]] = 0;
         }
+        if (in.cf != 0) a.bcnt[i] = 0;
     } else {
-        // each row's count and all 8 slots side by side (one L2 trip); slots
-        // past the count are ignored
-        int c[R], js[R][RL0_BUCKET];
-        float xv[R][RL0_BUCKET];
+        const int cb = cur ? in.c1 : in.c0;
+        const int4 b0 = cur ? in.b10 : in.b00, b1 = cur ? in.b11 : in.b01;
+        const int rb[RL0_BUCKET] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const int rf[RL0_BUCKET] = {in.f0.x, in.f0.y, in.f0.z, in.f0.w, in.f1.x, in.f1.y, in.f1.z, in.f1.w};
+        int js[2 * RL0_BUCKET];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            c[r] = 0;
-            yv[r] = 0.0f;
-            int4 b0 = make_int4(0, 0, 0, 0), b1 = b0;
-            if (has[r]) {
-                const RowIn in = pre ? pre[r] : load_row_inputs(a, ctx, i[r]);
-                c[r] = in.c;
-                b0 = in.b0;
-                b1 = in.b1;
-                yv[r] = in.y;
-            }
-            const int raw[RL0_BUCKET] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int q = 0; q < RL0_BUCKET; ++q) js[r][q] = (q < c[r]) ? raw[q] : 0x7fffffff;
+        for (int q = 0; q < RL0_BUCKET; ++q) {
+            js[q] = (q < cb) ? rb[q] : 0x7fffffff;
+            js[RL0_BUCKET + q] = (q < in.cf) ? rf[q] : 0x7fffffff;
         }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (c[r] > 1) sort8(js[r]);             // ascending column order
-#pragma unroll
-            for (int q = 0; q < RL0_BUCKET; ++q) xv[r][q] = (q < c[r]) ? x[js[r][q]] : 0.0f;
+        if (cb > 1) sort8(js);                      // ascending column order
+        if (in.cf > 0) {
+            if (in.cf > 1) sort8(js + RL0_BUCKET);
+            merge8x2(js);
         }
+        float xv[2 * RL0_BUCKET];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            sum[r] = 0.0f;
-            acc[r] = DF{yv[r], 0.0f};
+        for (int q = 0; q < 2 * RL0_BUCKET; ++q) xv[q] = (js[q] != 0x7fffffff) ? x[js[q]] : 0.0f;
 #pragma unroll
-            for (int q = 0; q < RL0_BUCKET; ++q)
-                if (q < c[r]) {
-                    sum[r] += xv[r][q];
-                    acc[r] = df_sub(acc[r], xv[r][q]);
+        for (int q = 0; q < 2 * RL0_BUCKET; ++q)
+            if (js[q] != 0x7fffffff) {
+                sum += xv[q];
+                acc = df_sub(acc, xv[q]);
+                if (xv[q] != 0.0f) {
+                    if (kept < RL0_BUCKET) nbkt[kept] = js[q];
+                    ++kept;
                 }
-            if (c[r] > 0) a.bcnt[i[r]] = 0;
-        }
+            }
+        if (in.cf != 0) a.bcnt[i] = 0;
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        l1[r] = DF{0.0f, 0.0f};
-        f1[r] = DF{0.0f, 0.0f};
-        if (!has[r]) continue;
-        const float rr = yv[r] - sum[r];
-        const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, rr);
-        rz[i[r]] = make_float2(rr, z);
-        if (a.res_ok) (cur ? a.code0 : a.code1)[i[r]] = residual_code(rr);
-        l1[r] = DF{fabsf(rr), 0.0f};
-        f1[r] = df_abs(acc[r]);
-    }
-}
-
-__device__ __forceinline__ void rebuild_row(const KArgs &a, const DecodeCtx *ctx, int i, bool csr, int cur, DF &l1,
-                                            DF &f1, const RowIn *pre = nullptr)
-{
-    const bool has = true;
-    rebuild_rows<1>(a, ctx, &i, &has, csr, cur, &l1, &f1, pre);
+    ncnt[i] = kept < RL0_BUCKET ? kept : RL0_BUCKET;
+    const float rr = in.y - sum;
+    const float z = ctx->indicator ? 0.0f : series_eval(ctx->pz, rr);
+    rz[i] = make_float2(rr, z);
+    if (a.res_ok) (cur ? a.code0 : a.code1)[i] = residual_code(rr);
+    l1 = DF{fabsf(rr), 0.0f};
+    f1 = df_abs(acc);
+    return kept <= RL0_BUCKET;
 }
 
 // ---------------------------------------------------------------------------
@@ -261,46 +356,65 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
     __shared__ DecodeState S;
     __shared__ double s_l1;
     __shared__ int s_acc;
+    __shared__ double s_parts[4 * NT];
     DecodeState *st = a.st;
     const int t = threadIdx.x;
     const DecodeCtx *ctx = a.ctx;
     float *x = ctx->x;
-    if (t < 32) {
-        if (t < SW) ((unsigned *)&S)[t] = __ldcg((const unsigned *)st + t);
-        double v = 0.0;
-        // ||r||_1 of the candidate: chunk partials combined in a fixed order
-        if (upd > 0) v = warp_sum_parts_l2(a.l1part, a.nchunks, t);
-        __syncwarp();
-        if (t == 0) {
-            S.rb_done = 0u;                        // the rebuild's last-CTA count starts over
-            s_l1 = v;
-            s_acc = (upd > 0) ? (ctx->always_accept ? 1 : (v < S.l1_hat)) : 0;
-        }
+    if (t < SW) ((unsigned *)&S)[t] = __ldcg((const unsigned *)st + t);
+    // ||r||_1 of the candidate: chunk partials combined in a fixed order
+    const double v = (upd > 0) ? cta_sum_parts_l2<NT>(a.l1part, a.nchunks, s_parts) : 0.0;
+    __syncthreads();
+    if (t == 0) {
+        S.rb_done = 0u;                            // the rebuild's last-CTA count starts over
+        s_l1 = v;
+        s_acc = (upd > 0) ? (ctx->always_accept ? 1 : (v < S.l1_hat)) : 0;
     }
     __syncthreads();
+    const int cur0 = S.cur;                        // r_hat's buffer during this round
     if (upd > 0) {
         if (s_acc) {
             if (S.drop_count > 0 || S.zeroed > 0) {
-                // entries became zero: stable in-place compaction of the list
+                // entries became zero: stable in-place compaction of the list,
+                // 4 NT entries at a time (each thread 4 consecutive ones; a warp
+                // scan of the per-thread counts, then one over the warps).
+                // Reading block b and writing its survivors below position
+                // 4 NT b cannot overwrite an unread entry.
+                constexpr int NW = NT / 32;
+                unsigned *wsum = shu;                 // NW words of scratch
                 const unsigned total = S.list_count;
+                const int lane = t & 31, warp = t >> 5;
                 unsigned out = 0;
-                for (unsigned base = 0; base < total; base += NT) {
-                    const unsigned e = base + t;
-                    int j = -1;
+                for (unsigned base = 0; base < total; base += 4 * NT) {
+                    int j[4];
                     unsigned keep = 0;
-                    if (e < total) { j = a.list[e]; keep = (x[j] != 0.0f); }
-                    shu[t] = keep;
-                    __syncthreads();
-                    for (int off = 1; off < NT; off <<= 1) {
-                        const unsigned w = (t >= off) ? shu[t - off] : 0u;
-                        __syncthreads();
-                        shu[t] += w;
-                        __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const unsigned e = base + 4 * t + q;
+                        j[q] = (e < total) ? __ldcg(a.list + e) : -1;
                     }
-                    const unsigned incl = shu[t];
-                    const unsigned blk = shu[NT - 1];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (j[q] >= 0 && __ldcg(x + j[q]) != 0.0f) keep |= 1u << q;
+                    const unsigned cnt = __popc(keep);
+                    unsigned incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned w = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += w;
+                    }
+                    if (lane == 31) wsum[warp] = incl;
                     __syncthreads();
-                    if (keep) a.list[out + incl - 1] = j;
+                    unsigned before = 0, blk = 0;
+                    for (int w = 0; w < NW; ++w) {
+                        const unsigned sw = wsum[w];
+                        if (w < warp) before += sw;
+                        blk += sw;
+                    }
+                    unsigned pos = out + before + incl - cnt;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if ((keep >> q) & 1u) a.list[pos++] = j[q];
                     out += blk;
                     __syncthreads();
                 }
@@ -336,7 +450,9 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
             a.rlog[round] = L;
         }
         if (upd > 0 && S.drop_count > 0) S.hk_rounds += 1;
-        if (upd > 0 && S.overflow) S.fallback_rounds += 1;
+        if (upd > 0 && (S.overflow || ((S.bflags >> cur0) & 1u))) S.fallback_rounds += 1;
+        // the next round's candidate support bucket starts out complete
+        S.bflags &= ~(1u << (S.cur ^ 1));
         S.upd_count = 0;
         S.drop_count = 0;
         S.overflow = 0;
@@ -359,12 +475,11 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
             S.done = 1;
     }
     __syncthreads();
-    if (S.done && t < 32) {
+    if (S.done) {
         // the decode ends here: ||y_hat - A x_hat||_1 from r_hat's chunk
         // partials, in k_final_sum's order
-        const double v = warp_sum_parts_l2(a.final_part + (size_t)S.cur * a.nchunks, a.nchunks, t);
-        if (t == 0) S.final_l1 = v;
-        __syncwarp();
+        const double fv = cta_sum_parts_l2<NT>(a.final_part + (size_t)S.cur * a.nchunks, a.nchunks, s_parts);
+        if (t == 0) S.final_l1 = fv;
     }
     __syncthreads();
     if (t < SW) ((unsigned *)st)[t] = ((const unsigned *)&S)[t];
