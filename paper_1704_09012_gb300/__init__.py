@@ -300,27 +300,41 @@ def round_step(A, y, k, round_index, xhat, rhat, want_passed=True, stream=None, 
     return xp, rp, passed, l1.value
 
 
+class BatchPlan:
+    """The argument arrays of one rl0_decode_batched call, marshalled once: As (list of
+    Expander), ys (CUDA float32 [m_i]), ks (ints), params (None, one dict for all, or one
+    dict per instance), outs (CUDA float32 [n_i], or None to allocate).  run() makes the
+    call and returns (list of x_hat, list of stats dicts); repeated runs reuse the arrays."""
+
+    def __init__(self, As, ys, ks, params=None, outs=None):
+        cnt = len(As)
+        if not (len(ys) == len(ks) == cnt):
+            raise ValueError("As, ys and ks must have the same length")
+        if params is None:
+            params = {}
+        plist = params if isinstance(params, (list, tuple)) else [params] * cnt
+        self.cnt = cnt
+        self.keep = (list(As), list(ys))
+        self.P = (Params * cnt)(*[make_params(**p) for p in plist])
+        self.xs = outs if outs is not None else [torch.empty(A.n, dtype=torch.float32, device="cuda") for A in As]
+        self.Ah = (C.c_void_p * cnt)(*[A.handle.value for A in As])
+        self.Yh = (C.c_void_p * cnt)(*[_dev(y, torch.float32, A.m, "y").value for A, y in zip(As, ys)])
+        self.Xh = (C.c_void_p * cnt)(*[_dev(x, torch.float32, A.n, "x_hat").value for A, x in zip(As, self.xs)])
+        self.K = (C.c_int64 * cnt)(*[int(k) for k in ks])
+        self.S = (Stats * cnt)()
+
+    def run(self, stream=None, stats=True):
+        _check(_lib().rl0_decode_batched(self.cnt, self.Ah, self.Yh, self.K, C.cast(self.P, C.c_void_p), self.Xh,
+                                         C.cast(self.S, C.c_void_p), _stream(stream)), "rl0_decode_batched")
+        return self.xs, ([s.as_dict() for s in self.S] if stats else None)
+
+
 def decode_batched(As, ys, ks, params=None, outs=None, stream=None):
     """Algorithm 2 on many independent instances in one persistent launch.
 
     As: list of Expander; ys: list of CUDA float32 [m_i]; ks: list of int; params: None, a
     dict applied to all, or a list of dicts.  Returns (list of x_hat, list of stats dicts)."""
-    cnt = len(As)
-    if not (len(ys) == len(ks) == cnt):
-        raise ValueError("As, ys and ks must have the same length")
-    if params is None:
-        params = {}
-    plist = params if isinstance(params, (list, tuple)) else [params] * cnt
-    P = (Params * cnt)(*[make_params(**p) for p in plist])
-    xs = outs if outs is not None else [torch.empty(A.n, dtype=torch.float32, device="cuda") for A in As]
-    Ah = (C.c_void_p * cnt)(*[A.handle.value for A in As])
-    Yh = (C.c_void_p * cnt)(*[_dev(y, torch.float32, A.m, "y").value for A, y in zip(As, ys)])
-    Xh = (C.c_void_p * cnt)(*[_dev(x, torch.float32, A.n, "x_hat").value for A, x in zip(As, xs)])
-    K = (C.c_int64 * cnt)(*[int(k) for k in ks])
-    S = (Stats * cnt)()
-    _check(_lib().rl0_decode_batched(cnt, Ah, Yh, K, C.cast(P, C.c_void_p), Xh, C.cast(S, C.c_void_p),
-                                     _stream(stream)), "rl0_decode_batched")
-    return xs, [s.as_dict() for s in S]
+    return BatchPlan(As, ys, ks, params, outs).run(stream)
 
 
 # ---------------------------------------------------------------------------

@@ -35,6 +35,7 @@
 
 #define RL0_BATCH_MAX_M 22528                       // rows held in shared memory (88 chunks)
 #define RL0_BATCH_MAX_CHUNKS (RL0_BATCH_MAX_M / RL0_ROWS_CHUNK)
+#define RL0_BATCH_QCAP 2048                         // queued columns held in shared memory
 
 struct BatchItem {
     int n, m, d, nrounds, nchunks, indicator;
@@ -52,6 +53,7 @@ struct BatchItem {
     UndoEntry *ulog, *dlog;
     int *bcnt, *bkt;
     unsigned long long *hkkey;
+    int *spill;                                     // queued columns beyond the shared queue: 2 ints each
 };
 
 struct BatchResult {
@@ -67,25 +69,100 @@ struct BatchState {
     double l1_hat, l1n, stop;
 };
 
+// The column bound of the single-instance column kernel (code_candidates2 in
+// rl0_device.cuh: two columns side by side in the FP16 lanes of half2
+// registers, every anchor and pair test taken on the residuals' 16-bit codes)
+// for columns a and b of exactly D rows, with the codes formed from r_hat
+// held in shared memory (code(r) = FP16(r) rounded toward zero; no clamp is
+// needed for finite r, since rounding toward zero never overflows) and n_z
+// exact: the p_z(r) values beside r_hat (0/1 scores: the count of |r| <= t_z)
+// summed in slot order, so the count test needs no lower-bound table.
+// Returns a superset of each column's anchors that pass Alg. 2's test.
+template <int D, bool IND>
+__device__ __forceinline__ void smem_candidates2(const float2 *s_rz, const int *ra, const int *rb, bool act_a,
+                                                 bool act_b, const CodeThr2 &ct, float tz, unsigned &ma,
+                                                 unsigned &mb)
+{
+    __half2 v[D];
+    __half2 vmax = __float2half2_rn(0.0f);
+    float nza = 0.0f, nzb = 0.0f;
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const float2 pa = s_rz[ra[s]], pb = s_rz[rb[s]];
+        v[s] = __halves2half2(__float2half_rz(pa.x), __float2half_rz(pb.x));
+        vmax = __hmax2(vmax, __habs2(v[s]));
+        nza += IND ? (fabsf(pa.x) <= tz ? 1.0f : 0.0f) : pa.y;
+        nzb += IND ? (fabsf(pb.x) <= tz ? 1.0f : 0.0f) : pb.y;
+    }
+    ma = mb = 0u;
+    const float va = __low2float(vmax), vb = __high2float(vmax);
+    const float ta = __low2float(ct.ta);
+    const bool any_a = act_a && va >= ta, any_b = act_b && vb >= ta;
+    if (!(any_a || any_b)) return;
+    const __half2 thr = __halves2half2(__float2half_ru(fmaf(va, ct.c1, ct.c0)), __float2half_ru(fmaf(vb, ct.c1, ct.c0)));
+    __half2 cnt[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s) cnt[s] = __float2half2_rn(0.0f);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+#pragma unroll
+        for (int l = s + 1; l < D; ++l) {
+            const __half2 q = __hle2(__habs2(__hsub2(v[s], v[l])), thr);
+            cnt[s] = __hadd2(cnt[s], q);
+            cnt[l] = __hadd2(cnt[l], q);
+        }
+    }
+    // candidate: near count >= need - 1 + n_z (rounded up to FP16: the count is exact)
+    const __half2 kneed = __halves2half2(__float2half_ru(ct.need1 + nza), __float2half_ru(ct.need1 + nzb));
+    unsigned anc = 0u, acc = 0u;
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+        const unsigned a = h2bits(__hge2(__habs2(v[s]), ct.ta)) & 0x04000400u;
+        const unsigned c = h2bits(__hge2(cnt[s], kneed));
+        anc |= a >> (10 - s);
+        acc |= (a & c) >> (10 - s);
+    }
+    // a saturated code (|v| = 65504 stands for every larger |r|): no bound
+    const unsigned fa = (va >= 65504.0f) ? anc : acc, fb = (vb >= 65504.0f) ? anc : acc;
+    ma = any_a ? (fa & 0xffffu) : 0u;
+    mb = any_b ? (fb >> 16) : 0u;
+}
+
+// Queue position q of a column that may pass: the shared queue, else the
+// instance's spill list (at most one entry per column, so it never fills).
+__device__ __forceinline__ void queue_push(int *qj, unsigned *qm, int *spill, int q, int j, unsigned mask)
+{
+    if (q < RL0_BATCH_QCAP) {
+        qj[q] = j;
+        qm[q] = mask;
+    } else {
+        spill[2 * (size_t)(q - RL0_BATCH_QCAP)] = j;
+        spill[2 * (size_t)(q - RL0_BATCH_QCAP) + 1] = (int)mask;
+    }
+}
+
 // __launch_bounds__(NT, 1): up to 65536/NT registers per thread.  With the
 // compiler's default target the column loop's row-id prefetch spilled; with
 // this bound no variant spills and a 2048-instance batch ran 19% faster.
-template <int DMAX, bool IND, int NT>
+template <int DMAX, bool IND, bool EXACT, int NT>
 __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__restrict__ items, BatchResult *results,
                                                        int count, int *queue)
 {
     constexpr int G = NT / RL0_ROWS_CHUNK;          // 256-row chunk groups per CTA
+    // exact d <= 8: two columns per thread per tile, bounded in FP16 lanes
+    constexpr bool PAIRED = EXACT && DMAX <= 8;
+    constexpr int CPT = PAIRED ? 2 : 1;             // columns per thread per tile
     extern __shared__ float2 s_rz[];                // r_hat, p_z(r_hat) of the current instance
     __shared__ BatchState S;
     __shared__ BatchItem I;
-    __shared__ float s_r[DMAX][NT];
-    __shared__ float s_nz[NT], s_rhs[NT];
-    __shared__ unsigned short s_q[NT];
-    __shared__ float s_score[NT], s_w[NT];
-    __shared__ unsigned char s_ok[NT];
+    __shared__ int s_qj[RL0_BATCH_QCAP];            // the round's queued columns
+    __shared__ unsigned s_qm[RL0_BATCH_QCAP];       // and their candidate slots
     __shared__ unsigned s_scan[NT];
     __shared__ DF s_red[NT];
     __shared__ double s_parts[RL0_BATCH_MAX_CHUNKS];
+    __shared__ double s_fpart[RL0_BATCH_MAX_CHUNKS];     // ||y - A x_hat||_1 chunk partials (FP32 pairs)
+    __shared__ double s_fcand[RL0_BATCH_MAX_CHUNKS];     // the same for the candidate x'
+    __shared__ DF s_red2[NT];
     __shared__ HkShared s_hk;
     __shared__ RoundThr s_th;
 
@@ -119,7 +196,7 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
                 v = DF{fabsf(r), 0.0f};
             }
             const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
-            if (gl == 0 && c < nchunks) s_parts[c] = sum;
+            if (gl == 0 && c < nchunks) s_parts[c] = s_fpart[c] = sum;   // x_hat = 0: both are ||y||_1's
         }
         bad = __syncthreads_or(bad);
         // ||r_hat||_1 in k_start's order (lane-strided, then a butterfly)
@@ -134,7 +211,8 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
             S.done = bad || S.converged || I.nrounds <= 0;
             S.round = 0;
             S.upd = S.list_count = S.shat_count = S.drop_count = S.nnz = S.zeroed = 0;
-            S.nnz_delta = S.overflow = S.nq = 0;
+            S.nnz_delta = S.overflow = 0;
+            S.nq = 0;
             S.accepted_rounds = S.hk_rounds = S.fallback_rounds = S.rounds_run = 0;
         }
         __syncthreads();
@@ -145,82 +223,132 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
             const RoundThr th = s_th;
             const float alpha = I.alpha;
 
-            // ---- column scores (same arithmetic as k_column_score); the row
-            // ids of the next tile are loaded while this one is scored
-            int nxt[DMAX];
+            // ---- column scores.
+            // Stream: each thread bounds its columns' anchors (smem_candidates2
+            // for exact d <= 8, else anchor_candidates on the FP32 residuals)
+            // and queues the columns that may pass (a few in a thousand: the
+            // first RL0_BATCH_QCAP in shared memory, the rest in the
+            // instance's spill list); the row ids of the next tile load while
+            // a tile is bounded; no thread waits on another.
+            // Resolve, once per round: one thread per queued column scores its
+            // candidate slots exactly, highest first (score_anchor's arithmetic:
+            // the first to pass is the last passing anchor in row order), and
+            // commits.
+            const CodeThr2 ct2 = code_thresholds2(code_thresholds(th.ta, th.tz, IND ? th.te : I.pe.cut),
+                                                  IND ? alpha : alpha - 1e-3f);
+            int nxa[DMAX], nxb[PAIRED ? DMAX : 1];
 #pragma unroll
-            for (int s = 0; s < DMAX; ++s) nxt[s] = (s < d && tid < n) ? __ldg(I.rows_sm + (size_t)s * n + tid) : 0;
-            for (int base = 0; base < n; base += NT) {
-                const int j = base + tid;
-                const bool active = j < n;
-                int rid[DMAX];
+            for (int s = 0; s < DMAX; ++s) {
+                nxa[s] = (s < d && tid < n) ? __ldg(I.rows_sm + (size_t)s * n + tid) : 0;
+                if constexpr (PAIRED) nxb[s] = (tid + NT < n) ? __ldg(I.rows_sm + (size_t)s * n + tid + NT) : 0;
+            }
+            {
+                for (int base = 0; base < n; base += NT * CPT) {
+                    const int ja = base + tid, jb = ja + NT;
+                    int ra[DMAX], rb[PAIRED ? DMAX : 1];
 #pragma unroll
-                for (int s = 0; s < DMAX; ++s) {
-                    rid[s] = nxt[s];
-                    if (s < d && j + NT < n) nxt[s] = __ldg(I.rows_sm + (size_t)s * n + j + NT);
-                }
-                float r[DMAX];
-                float nz = 0.0f, rhs = 0.0f;
+                    for (int s = 0; s < DMAX; ++s) {
+                        ra[s] = nxa[s];
+                        if constexpr (PAIRED) rb[s] = nxb[s];
+                    }
+                    {
+                        const int jn = base + NT * CPT + tid;
 #pragma unroll
-                for (int s = 0; s < DMAX; ++s) {
-                    r[s] = 0.0f;
-                    if (s < d && active) {
-                        const float2 v = s_rz[rid[s]];
-                        r[s] = v.x;
-                        nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
-                        rhs += fabsf(v.x);
+                        for (int s = 0; s < DMAX; ++s) {
+                            if (s < d && jn < n) nxa[s] = __ldg(I.rows_sm + (size_t)s * n + jn);
+                            if constexpr (PAIRED)
+                                if (jn + NT < n) nxb[s] = __ldg(I.rows_sm + (size_t)s * n + jn + NT);
+                        }
+                    }
+                    unsigned ma = 0u, mb = 0u;
+                    if constexpr (PAIRED) {
+                        smem_candidates2<DMAX, IND>(s_rz, ra, rb, ja < n, jb < n, ct2, th.tz, ma, mb);
+                    } else if (ja < n) {
+                        float r[DMAX];
+                        float nz = 0.0f;
+#pragma unroll
+                        for (int s = 0; s < DMAX; ++s) {
+                            r[s] = 0.0f;
+                            if (s < d) {
+                                const float2 v = s_rz[ra[s]];
+                                r[s] = v.x;
+                                nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
+                            }
+                        }
+                        ma = anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, I.pe_b1, I.pe_c1, nz,
+                                                          IND ? alpha : alpha - 1e-3f);
+                    }
+                    const unsigned ba = __ballot_sync(0xffffffffu, ma != 0u);
+                    const unsigned bb = PAIRED ? __ballot_sync(0xffffffffu, mb != 0u) : 0u;
+                    if (ba | bb) {
+                        const int leader = __ffs(ba | bb) - 1;
+                        int q0 = 0;
+                        if (lane == leader) q0 = atomicAdd(&S.nq, __popc(ba) + __popc(bb));
+                        q0 = __shfl_sync(0xffffffffu, q0, leader);
+                        const unsigned lt = (1u << lane) - 1u;
+                        if (ma) queue_push(s_qj, s_qm, I.spill, q0 + __popc(ba & lt), ja, ma);
+                        if (PAIRED && mb) queue_push(s_qj, s_qm, I.spill, q0 + __popc(ba) + __popc(bb & lt), jb, mb);
                     }
                 }
-                unsigned cand = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, I.pe_b1,
-                                                                      I.pe_c1, nz, IND ? alpha : alpha - 1e-3f)
-                                       : 0u;
-                if (cand) {
+                __syncthreads();
+                const int nq = S.nq;
+                for (int e = tid; e < nq; e += NT) {
+                    int j;
+                    unsigned cm;
+                    if (e < RL0_BATCH_QCAP) {
+                        j = s_qj[e];
+                        cm = s_qm[e];
+                    } else {
+                        j = __ldcg(I.spill + 2 * (size_t)(e - RL0_BATCH_QCAP));
+                        cm = (unsigned)__ldcg(I.spill + 2 * (size_t)(e - RL0_BATCH_QCAP) + 1);
+                    }
+                    float r[DMAX];
+                    float nz = 0.0f, rhs = 0.0f;
+                    unsigned cand = 0u;
 #pragma unroll
-                    for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
-                    s_nz[tid] = nz;
-                    s_rhs[tid] = rhs;
-                }
-                int best = -1;
-                float bw = 0.0f;
-                while (__syncthreads_or(cand != 0u)) {
-                    int my = -1, ms = 0;
-                    if (cand) {
-                        ms = 31 - __clz(cand);      // highest remaining slot first
-                        cand &= ~(1u << ms);
-                        my = atomicAdd(&S.nq, 1);
-                        s_q[my] = (unsigned short)((tid << 5) | ms);
+                    for (int s = 0; s < DMAX; ++s) {
+                        r[s] = 0.0f;
+                        if (s < d) {
+                            const float2 v = s_rz[__ldg(I.rows_sm + (size_t)s * n + j)];
+                            r[s] = v.x;
+                            nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
+                            rhs += fabsf(v.x);
+                            if (((cm >> s) & 1u) && fabsf(v.x) >= th.ta) cand |= 1u << s;
+                        }
                     }
-                    __syncthreads();
-                    const int nq = S.nq;
-                    for (int e = tid; e < nq; e += NT) {
-                        const int owner = s_q[e] >> 5, s = s_q[e] & 31;
-                        float sc, w;
-                        s_ok[e] = score_anchor<IND>(&s_r[0][owner], NT, d, s, th.te, I.pe, s_nz[owner],
-                                                    s_rhs[owner], alpha, &sc, &w) ? 1 : 0;
-                        s_score[e] = sc;
-                        s_w[e] = w;
+                    // the FP32 bound (exact near counts; continuous scores: an upper
+                    // bound of each q_e) before the exact evaluation
+                    if (cand)
+                        cand &= anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : I.pe.cut, I.pe_b1, I.pe_c1,
+                                                             nz, IND ? alpha : alpha - 1e-3f);
+                    int best = -1;
+                    float bw = 0.0f;
+                    while (cand) {
+                        const int s = 31 - __clz(cand);
+                        cand &= ~(1u << s);
+                        const AnchorEval E = eval_anchor_regs<DMAX, IND>(r, d, s, th.te, I.pe);
+                        if (E.lhs <= rhs && E.ne - nz >= alpha) {
+                            best = s;
+                            bw = E.w;
+                            break;
+                        }
                     }
-                    __syncthreads();
-                    if (my >= 0 && s_ok[my]) {      // first pass from the top = last passing anchor
-                        best = ms;
-                        bw = s_w[my];
-                        cand = 0u;
+                    if (best >= 0) {
+                        const float old = x[j];
+                        const float nv = old + bw;
+                        x[j] = nv;
+                        const int dn = (int)(nv != 0.0f) - (int)(old != 0.0f);
+                        if (dn) atomicAdd(&S.nnz_delta, dn);
+                        if (old != 0.0f && nv == 0.0f) atomicAdd(&S.zeroed, 1u);
+                        UndoEntry u;
+                        u.j = j;
+                        u.old = old;
+                        I.ulog[atomicAdd(&S.upd, 1u)] = u;
+                        if (old == 0.0f && nv != 0.0f) I.list[atomicAdd(&S.list_count, 1u)] = j;
                     }
-                    if (tid == 0) S.nq = 0;
                 }
-                if (best >= 0) {
-                    const float old = x[j];
-                    const float nv = old + bw;
-                    x[j] = nv;
-                    const int dn = (int)(nv != 0.0f) - (int)(old != 0.0f);
-                    if (dn) atomicAdd(&S.nnz_delta, dn);
-                    if (old != 0.0f && nv == 0.0f) atomicAdd(&S.zeroed, 1u);
-                    UndoEntry u;
-                    u.j = j;
-                    u.old = old;
-                    I.ulog[atomicAdd(&S.upd, 1u)] = u;
-                    if (old == 0.0f && nv != 0.0f) I.list[atomicAdd(&S.list_count, 1u)] = j;
-                }
+                __syncthreads();
+                if (tid == 0) S.nq = 0;                 // next read after the round's later barriers
             }
             __syncthreads();
             const unsigned upd = S.upd;
@@ -242,36 +370,112 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
                     else S.overflow = 1;
                 }
                 __syncthreads();
-                // ---- rebuild r = y - A x' (same order as k_rebuild)
+                // ---- rebuild r = y - A x' (k_rebuild's arithmetic): one warp per
+                // 256-row chunk, lane l taking rows l + 32 q (q < 8); the chunk's
+                // two sums are the tree of group_sum2_df, formed inside the warp
+                // (the same additions in the same order), so no CTA barrier waits
+                // on the slowest row
                 const bool csr = S.overflow != 0;
-                for (int cb = 0; cb < nchunks; cb += G) {
-                    const int c = cb + grp, i = c * RL0_ROWS_CHUNK + gl;
-                    DF v{0.0f, 0.0f};
-                    if (c < nchunks && i < m) {
-                        float sum = 0.0f;
-                        if (csr) {
-                            for (int p = I.rowptr[i]; p < I.rowptr[i + 1]; ++p) sum += x[I.colidx[p]];
-                            I.bcnt[i] = 0;
-                        } else {
-                            const int cnt = I.bcnt[i];
-                            if (cnt > 0) {
-                                int js[RL0_BUCKET];
+                for (int c = tid >> 5; c < nchunks; c += NT / 32) {
+                    DF v[8], v2[8];
+                    // four rows at a time: their loads are all issued before
+                    // any of their stores
 #pragma unroll
-                                for (int q = 0; q < RL0_BUCKET; ++q)
-                                    js[q] = (q < cnt) ? I.bkt[(long long)i * RL0_BUCKET + q] : 0x7fffffff;
-                                sort8(js);
+                    for (int h = 0; h < 8; h += 4) {
+                        int cnt[4];
+                        int4 b0[4], b1[4];
+                        float yv[4];
 #pragma unroll
-                                for (int q = 0; q < RL0_BUCKET; ++q)
-                                    if (q < cnt) sum += x[js[q]];
-                                I.bcnt[i] = 0;
+                        for (int q = 0; q < 4; ++q) {
+                            const int i = c * RL0_ROWS_CHUNK + lane + 32 * (h + q);
+                            cnt[q] = 0;
+                            yv[q] = 0.0f;
+                            b0[q] = b1[q] = make_int4(0, 0, 0, 0);
+                            if (i < m) {
+                                yv[q] = I.y[i];
+                                if (!csr) {
+                                    cnt[q] = I.bcnt[i];
+                                    const int4 *bq = (const int4 *)(I.bkt + (long long)i * RL0_BUCKET);
+                                    b0[q] = bq[0];
+                                    b1[q] = bq[1];
+                                }
                             }
                         }
-                        const float r = I.y[i] - sum;
-                        I.rzc[i] = make_float2(r, I.indicator ? 0.0f : series_eval(I.pz, r));
-                        v = DF{fabsf(r), 0.0f};
+                        float sum[4];
+                        DF acc[4];
+                        if (csr) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int i = c * RL0_ROWS_CHUNK + lane + 32 * (h + q);
+                                sum[q] = 0.0f;
+                                acc[q] = DF{yv[q], 0.0f};
+                                if (i < m)
+                                    for (int p = I.rowptr[i]; p < I.rowptr[i + 1]; ++p) {
+                                        const float xv = x[I.colidx[p]];
+                                        sum[q] += xv;
+                                        acc[q] = df_sub(acc[q], xv);
+                                    }
+                            }
+                        } else {
+                            float xs[4][RL0_BUCKET];
+                            int js[4][RL0_BUCKET];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int raw[RL0_BUCKET] = {b0[q].x, b0[q].y, b0[q].z, b0[q].w,
+                                                             b1[q].x, b1[q].y, b1[q].z, b1[q].w};
+#pragma unroll
+                                for (int u = 0; u < RL0_BUCKET; ++u) js[q][u] = (u < cnt[q]) ? raw[u] : 0x7fffffff;
+                                if (cnt[q] > 1) sort8(js[q]);
+#pragma unroll
+                                for (int u = 0; u < RL0_BUCKET; ++u) xs[q][u] = (u < cnt[q]) ? x[js[q][u]] : 0.0f;
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                sum[q] = 0.0f;
+                                acc[q] = DF{yv[q], 0.0f};
+#pragma unroll
+                                for (int u = 0; u < RL0_BUCKET; ++u)
+                                    if (u < cnt[q]) {
+                                        sum[q] += xs[q][u];
+                                        acc[q] = df_sub(acc[q], xs[q][u]);
+                                    }
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int i = c * RL0_ROWS_CHUNK + lane + 32 * (h + q);
+                            v[h + q] = DF{0.0f, 0.0f};
+                            v2[h + q] = DF{0.0f, 0.0f};
+                            if (i < m) {
+                                if (csr || cnt[q] > 0) I.bcnt[i] = 0;
+                                const float r = yv[q] - sum[q];
+                                I.rzc[i] = make_float2(r, I.indicator ? 0.0f : series_eval(I.pz, r));
+                                v[h + q] = DF{fabsf(r), 0.0f};
+                                v2[h + q] = df_abs(acc[q]);
+                            }
+                        }
                     }
-                    const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
-                    if (gl == 0 && c < nchunks) s_parts[c] = sum;
+                    // levels 128, 64, 32 of the chunk's tree, then its warp shuffles
+                    DF a0 = df_add(v[0], v[4]), a1 = df_add(v[1], v[5]), a2 = df_add(v[2], v[6]), a3 = df_add(v[3], v[7]);
+                    DF e0 = df_add(v2[0], v2[4]), e1 = df_add(v2[1], v2[5]), e2 = df_add(v2[2], v2[6]),
+                       e3 = df_add(v2[3], v2[7]);
+                    a0 = df_add(a0, a2);
+                    a1 = df_add(a1, a3);
+                    e0 = df_add(e0, e2);
+                    e1 = df_add(e1, e3);
+                    DF ra = df_add(a0, a1), rb = df_add(e0, e1);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const DF ua = df_shfl_down(ra, off), ub = df_shfl_down(rb, off);
+                        if (lane < off) {
+                            ra = df_add(ra, ua);
+                            rb = df_add(rb, ub);
+                        }
+                    }
+                    if (lane == 0) {
+                        s_parts[c] = df_to_double(ra);
+                        s_fcand[c] = df_to_double(rb);
+                    }
                 }
                 __syncthreads();
                 // ---- accept: ||r||_1 < ||r_hat||_1 (same combination as k_accept)
@@ -307,6 +511,7 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
                         if (tid == 0) S.list_count = out;
                     }
                     for (int i = tid; i < m; i += NT) s_rz[i] = I.rzc[i];
+                    for (int c = tid; c < nchunks; c += NT) s_fpart[c] = s_fcand[c];
                     if (tid == 0) {
                         S.shat_count = S.list_count;
                         S.nnz = (unsigned)((int)S.nnz + S.nnz_delta - (int)S.drop_count);
@@ -338,21 +543,11 @@ __global__ void __launch_bounds__(NT, 1) k_decode_batched(const BatchItem *__res
             __syncthreads();
         }
 
-        // ---- ||y - A x_hat||_1 in FP32 pairs (same chunks and combination as the single decode)
-        for (int cb = 0; cb < nchunks; cb += G) {
-            const int c = cb + grp, i = c * RL0_ROWS_CHUNK + gl;
-            DF v{0.0f, 0.0f};
-            if (c < nchunks && i < m) {
-                DF acc{I.y[i], 0.0f};
-                for (int p = I.rowptr[i]; p < I.rowptr[i + 1]; ++p) acc = df_sub(acc, x[I.colidx[p]]);
-                v = df_abs(acc);
-            }
-            const double sum = group_sum_df(v, s_red + grp * RL0_ROWS_CHUNK, gl, RL0_ROWS_CHUNK);
-            if (gl == 0 && c < nchunks) s_parts[c] = sum;
-        }
+        // ---- ||y - A x_hat||_1 in FP32 pairs: the accepted rebuild's chunk partials
+        // (same chunks and combination as the single decode)
         __syncthreads();
         if (tid < 32) {
-            const double fl = warp_sum_parts(s_parts, nchunks, lane);
+            const double fl = warp_sum_parts(s_fpart, nchunks, lane);
             if (tid == 0) {
                 BatchResult R;
                 R.rounds = S.rounds_run;
@@ -383,17 +578,27 @@ struct Variant {
     int nt;
 };
 
-template <int DMAX, bool IND, int NT>
-Variant variant() { return Variant{k_decode_batched<DMAX, IND, NT>, NT}; }
+template <int DMAX, bool IND, bool EXACT, int NT>
+Variant variant() { return Variant{k_decode_batched<DMAX, IND, EXACT, NT>, NT}; }
 
-// Candidate schedules for a (DMAX, score kind): threads per CTA.
-std::vector<Variant> variants(int dmax, int ind)
+// Kernel group of column degree d: the exact-d kernels (two columns per thread
+// in FP16 lanes) for 6 <= d <= 8, else the smallest DMAX >= d.
+int batch_group(int d) { return (d >= 6 && d <= 8) ? d : (d < 6 ? 9 : (d <= 16 ? 16 : 32)); }
+
+// Candidate schedules for a (group, score kind): threads per CTA.
+std::vector<Variant> variants(int grp, int ind)
 {
     std::vector<Variant> v;
-#define RL0_V(D, I) { v.push_back(variant<D, I, 256>()); v.push_back(variant<D, I, 512>()); }
-    if (dmax == 8) { if (ind) RL0_V(8, true) else RL0_V(8, false) }
-    else if (dmax == 16) { if (ind) RL0_V(16, true) else RL0_V(16, false) }
-    else { if (ind) v.push_back(variant<32, true, 256>()); else v.push_back(variant<32, false, 256>()); }
+#define RL0_V(D, I, E) { v.push_back(variant<D, I, E, 256>()); v.push_back(variant<D, I, E, 512>()); }
+    switch (grp) {
+    case 6: if (ind) RL0_V(6, true, true) else RL0_V(6, false, true) break;
+    case 7: if (ind) RL0_V(7, true, true) else RL0_V(7, false, true) break;
+    case 8: if (ind) RL0_V(8, true, true) else RL0_V(8, false, true) break;
+    case 9: if (ind) RL0_V(8, true, false) else RL0_V(8, false, false) break;
+    case 16: if (ind) RL0_V(16, true, false) else RL0_V(16, false, false) break;
+    default:
+        if (ind) v.push_back(variant<32, true, false, 256>()); else v.push_back(variant<32, false, false, 256>());
+    }
 #undef RL0_V
     return v;
 }
@@ -509,11 +714,26 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
     if (e) return e;
     std::vector<DecodeCtx> ctx(count);
     {
+        // tables each expander's cache does not hold are built by a pool of
+        // host threads (a few tens of microseconds each); the rest are copies
+        std::vector<int> miss;
+        std::vector<char> is_miss(count, 0);
+        for (int i = 0; i < count; ++i)
+            if (!rl0_tables_cached(A[i], k[i], R[i])) {
+                miss.push_back(i);
+                is_miss[i] = 1;
+            }
         const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-        const int nth = (int)std::min<unsigned>(hw, (unsigned)std::max(1, count / 8));
+        const int nth = (int)std::min<unsigned>(hw, (unsigned)std::max<size_t>(1, miss.size() / 16));
         auto work = [&](int t0) {
-            for (int i = t0; i < count; i += nth)
-                rl0::fill_tables(A[i]->m, A[i]->d, k[i], R[i], &ctx[i], B.h_thr + thr_off[i], R[i].nrounds);
+            for (size_t q = t0; q < miss.size(); q += nth) {
+                const int i = miss[q];
+                rl0_cached_tables(const_cast<rl0_expander *>(A[i]), k[i], R[i], &ctx[i], B.h_thr + thr_off[i]);
+            }
+            if (t0 == 0)
+                for (int i = 0; i < count; ++i)
+                    if (!is_miss[i])
+                        rl0_cached_tables(const_cast<rl0_expander *>(A[i]), k[i], R[i], &ctx[i], B.h_thr + thr_off[i]);
         };
         std::vector<std::thread> pool;
         for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
@@ -521,7 +741,7 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
         for (auto &th : pool) th.join();
     }
     // ---- descriptors, grouped by (DMAX, score kind), largest work first
-    auto dmax_of = [](int d) { return d <= 8 ? 8 : (d <= 16 ? 16 : 32); };
+    auto dmax_of = batch_group;
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) {
@@ -564,6 +784,7 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
         It.bcnt = X->ws.bcnt;
         It.bkt = X->ws.bkt;
         It.hkkey = X->ws.hk_scratch;
+        It.spill = X->ws.res_list;                  // n entries of at least 2 ints
     }
     CK(cudaMemcpyAsync(B.d_items, B.h_items, count * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.d_thr, B.h_thr, thr_off[count] * sizeof(RoundThr), cudaMemcpyHostToDevice, s));

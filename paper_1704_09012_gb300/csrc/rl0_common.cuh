@@ -218,6 +218,9 @@ void rl0_expander_release(rl0_expander *A);
 // Decode workspace (rl0_decode.cu).
 int rl0_workspace_alloc(rl0_expander *A);
 void rl0_workspace_free(rl0_expander *A);
+// Host tables of (k, R) for A, cached per expander (rl0_decode.cu).
+void rl0_cached_tables(rl0_expander *A, int64_t k, const rl0::Resolved &R, DecodeCtx *ctx, RoundThr *thr);
+bool rl0_tables_cached(const rl0_expander *A, int64_t k, const rl0::Resolved &R);
 
 static inline unsigned rl0_div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 

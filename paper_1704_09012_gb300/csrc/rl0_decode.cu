@@ -902,6 +902,21 @@ static void cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeC
     }
 }
 
+// The same for other translation units (the batched decoder): the tables of
+// (k, R) for expander A, from its cache when they repeat the last call's.
+// Calls for distinct expanders may run concurrently.
+void rl0_cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr)
+{
+    cached_tables(A, k, R, ctx, thr);
+}
+
+// Whether A's cache holds the tables of (k, R).
+bool rl0_tables_cached(const rl0_expander *A, int64_t k, const Resolved &R)
+{
+    const TableCache *tc = (const TableCache *)A->table_cache;
+    return tc && tc->valid && tc->k == k && tc->nrounds == R.nrounds && same_params(tc->p, R.p);
+}
+
 // p_z lower bounds of the parameter set cached_tables just resolved.
 static void cached_pz(rl0_expander *A, int64_t k, const Resolved &R, float *out)
 {
