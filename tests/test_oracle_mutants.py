@@ -60,6 +60,8 @@ MUTANTS = [
      "if (!dup) col[got++] = cand;", "col[got++] = cand;"),
     ("quantised q_z test reversed",
      "return (lp >= lim) ? 1.0 : 0.0;", "return (lp <= lim) ? 1.0 : 0.0;"),
+    ("quantised q_e thresholded at 1 - t in place of t",
+     "return (lp >= log(t)) ? 1.0 : 0.0;", "return (lp >= log(1.0 - t)) ? 1.0 : 0.0;"),
     ("learned scorer: second hidden layer without its ReLU",
      "out += (a > 0.0 ? a : 0.0) * w3[o];", "out += a * w3[o];"),
     ("learned scorer: first weight matrix read transposed",

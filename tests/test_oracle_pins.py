@@ -436,3 +436,45 @@ def test_the_consensus_averages_the_rows_noise(quantised):
     assert moved.size >= 0.8 * iso.size
     rms = math.sqrt(np.mean((xp[moved] - I.x[moved]) ** 2))
     assert rms < 0.7 * sn, rms / sn
+
+
+def test_quantised_pair_test_counts_a_pair_when_its_posterior_reaches_t():
+    """Table "scores", quantised: a pair (r_s, r_l) counts towards n_e when
+    p_e(r_s - r_l) >= t.  Worked case: one column of d = 3 rows whose residuals are
+    (a, a + D, a - D), a = 1 far above the noise (every row an anchor, no row a zero:
+    p_z is below 1e-6), D where the posterior p_e (pinned against the model by Monte
+    Carlo above) equals 0.5, so p_e(2 D) < 0.3.  At t = 0.3 a pair at distance D
+    counts (0.5 >= 0.3) and one at 2 D does not: the last anchor in row order, a - D,
+    has n_e = 2 (itself and a), n_e - n_z = 2 >= alpha = 2, the l1 test holds, and the
+    column takes omega = (a + (a - D)) / 2.  At t = 0.7 no pair counts (0.5 < 0.7):
+    every anchor has n_e - n_z = 1 and the column keeps x_j.  Reading the threshold as
+    1 - t would give the opposite outcome in both rounds."""
+    d, sigma_n = 3, 1e-2
+    rows = np.array([[0, 1, 2]], np.int32)
+    k, m = 1, 3
+    rho = k / m
+    # D with p_e(D) = 1/2, by bisection on the (Monte-Carlo-pinned) posterior
+    lo, hi = 0.0, 20.0 * sigma_n
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if oracle.log_posterior("e", mid, d, rho, 1.0, sigma_n)[0] > math.log(0.5):
+            lo = mid
+        else:
+            hi = mid
+    D = 0.5 * (lo + hi)
+    assert 0.5 * sigma_n < D < 10 * sigma_n
+    a = 1.0
+    r = np.array([a, a + D, a - D])
+    assert np.exp(oracle.log_posterior("z", r, d, rho, 1.0, sigma_n)).max() < 1e-6
+    assert np.exp(oracle.log_posterior("e", 2 * D, d, rho, 1.0, sigma_n))[0] < 0.3
+    y = r.copy()                                         # x_hat = 0: r_hat = y
+    c = 0.1
+    for t, passes in ((0.3, True), (0.7, False)):
+        ridx = int(round((1.0 - t) / c))
+        xp, _, upd, rec = oracle.round_step(rows, y, k, ridx, np.zeros(1), r, sigma_n=sigma_n, quantised=True, c=c)
+        assert bool(rec["passed"][0]) == passes, t
+        if passes:
+            assert rec["best_slot"][0] == 2
+            assert rec["omega"][0] == pytest.approx(a - D / 2, rel=1e-12)
+            assert xp[0] == rec["omega"][0]
+            assert rec["score"][0] == 2.0
