@@ -66,6 +66,13 @@ typedef struct {
     double noiseless_tol;  /* sigma_n = 0: |a - b| <= tol counts as equal; 0 = 1e-5           */
     int    profile;        /* 1: time each kernel group with CUDA events captured into the    */
                            /* round graph and report it in rl0_stats.ms_* (adds event nodes)  */
+    int    anchor_rule;    /* the update a column takes when several of its anchors pass      */
+                           /* Algorithm 2's test (the paper adds one per anchor; one update   */
+                           /* per column is kept): 0 = the last passing anchor in row order   */
+                           /* (Alg. 1's overwrite), 1 = the one with the largest n_e - n_z,   */
+                           /* ties to the lower row.  1 is for comparing the two readings:    */
+                           /* the batched decoder, the learned scorer and rl0_decode_static   */
+                           /* return RL0_ERR_UNSUPPORTED with it                              */
 } rl0_params;
 
 /* Per-decode statistics (host structure filled by the library). */

@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("learned", C.c_int),
         ("mlp", C.c_void_p),
         ("mlp_threshold", C.c_double),
+        ("best_anchor", C.c_int),
     ]
 
 
@@ -204,7 +205,7 @@ _keep = []
 
 def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell=0,
                 max_rounds=0, noiseless_tol=0.0, literal_ei_test=False, mlp_bf16=None, mlp_threshold=0.0,
-                adaptive_k=False):
+                adaptive_k=False, best_anchor=False):
     """mlp_bf16: the learned scorer's parameters as a uint16 array of BF16 bit patterns
     (enables the learned rule); None keeps Algorithm 2's analytic rule."""
     ptr = None
@@ -214,7 +215,8 @@ def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell
         del _keep[:-8]
         ptr = arr.ctypes.data
     return Params(sigma_s, sigma_n, int(quantised), int(adaptive_k), c, alpha, ell, max_rounds,
-                  noiseless_tol, int(literal_ei_test), int(mlp_bf16 is not None), ptr, mlp_threshold)
+                  noiseless_tol, int(literal_ei_test), int(mlp_bf16 is not None), ptr, mlp_threshold,
+                  int(best_anchor))
 
 
 def decode(rows, yhat, k, log_cap=256, **kw):

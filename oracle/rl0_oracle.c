@@ -327,6 +327,9 @@ typedef struct {
     int learned;          /* 1: the learned column scorer replaces n_e - n_z >= alpha */
     const uint16_t *mlp;  /* its parameters as BF16 bit patterns (1633 values)   */
     double mlp_threshold; /* accept when sigmoid(logit) >= this; 0 = 0.5        */
+    int best_anchor;      /* 1: of a column's passing anchors, the one with the
+                             largest n_e - n_z (ties: the lower row) gives the
+                             update; 0: the last passing one in row order     */
 } orc_params;
 
 typedef struct {
@@ -550,7 +553,8 @@ typedef struct {
  *  - the update x'_j <- x'_j + w is applied once per column, because every
  *    member of a consensus group passes the test and would otherwise add w up
  *    to d times; the value is that of the last passing anchor in row order,
- *    the overwrite semantics of Alg. 1's u_j <- r_i;
+ *    the overwrite semantics of Alg. 1's u_j <- r_i (best_anchor = 1: the
+ *    passing anchor with the largest n_e - n_z, the lower row on ties);
  *  - ||r - w e_i||_1 <= ||r||_1 is read over the column's rows N(j):
  *    sum_l |r_l - w| <= sum_l |r_l|, the l1 change that adding w to x_j
  *    alone would cause (literal_ei_test = 1 keeps the printed |r_i - w| <= |r_i|);
@@ -632,7 +636,11 @@ int orc_round_step(int64_t n, int64_t m, int d, const int32_t *rows, const doubl
                     if (lg >= lt) { best = s; best_score = lg; best_w = w; }
                 }
             } else if (lhs <= rhs && score >= p->alpha) {
-                best = s; best_score = score; best_w = w;
+                /* rows come in ascending order: the last passing anchor, or
+                 * (best_anchor) the first of the largest score */
+                if (!p->best_anchor || best < 0 || score > best_score) {
+                    best = s; best_score = score; best_w = w;
+                }
             }
         }
         if (best >= 0) { xp[j] = xh[j] + best_w; upd++; }

@@ -51,7 +51,7 @@ class Params(C.Structure):
         ("sigma_s", C.c_double), ("sigma_n", C.c_double), ("quantised", C.c_int), ("adaptive_k", C.c_int),
         ("c", C.c_double), ("alpha", C.c_double), ("ell", C.c_int), ("scorer", C.c_int),
         ("mlp", C.c_void_p), ("mlp_threshold", C.c_double), ("max_rounds", C.c_int),
-        ("noiseless_tol", C.c_double), ("profile", C.c_int),
+        ("noiseless_tol", C.c_double), ("profile", C.c_int), ("anchor_rule", C.c_int),
     ]
 
 
@@ -144,10 +144,10 @@ def _dev(t, dtype, n=None, what="tensor"):
 
 
 def make_params(sigma_s=1.0, sigma_n=0.0, quantised=False, c=0.0, alpha=0.0, ell=0, scorer=0, mlp=None,
-                mlp_threshold=0.0, max_rounds=0, noiseless_tol=0.0, adaptive_k=False, profile=False):
+                mlp_threshold=0.0, max_rounds=0, noiseless_tol=0.0, adaptive_k=False, profile=False, anchor_rule=0):
     mlp_ptr = mlp.data_ptr() if isinstance(mlp, torch.Tensor) else mlp
     return Params(sigma_s, sigma_n, int(quantised), int(adaptive_k), c, alpha, ell, scorer, mlp_ptr,
-                  mlp_threshold, max_rounds, noiseless_tol, int(profile))
+                  mlp_threshold, max_rounds, noiseless_tol, int(profile), int(anchor_rule))
 
 
 class Expander:

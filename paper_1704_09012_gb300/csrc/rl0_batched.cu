@@ -705,7 +705,7 @@ extern "C" int rl0_decode_batched(int count, const rl0_expander *const *A, const
         if (rc[i]) return rc[i];
         // the learned scorer and adaptive_k (a host step after every accepted
         // round) do not fit one persistent launch
-        if (R[i].p.scorer == 1 || R[i].p.adaptive_k) return RL0_ERR_UNSUPPORTED;
+        if (R[i].p.scorer == 1 || R[i].p.adaptive_k || R[i].p.anchor_rule != 0) return RL0_ERR_UNSUPPORTED;
         thr_off[i + 1] = thr_off[i] + R[i].nrounds;
     }
     std::lock_guard<std::mutex> lock(g_buf_mutex);

@@ -105,6 +105,7 @@ struct ResScratch {
     unsigned char it_s[NT * DMAX];       // item -> slot (descending within a column)
     unsigned char it_ok[NT * DMAX];
     float it_w[NT * DMAX];
+    float it_sc[NT * DMAX];              // n_e - n_z of the item
     float q[NT][DMAX];                   // q_e of (item, slot l), NT items at a time
     unsigned wsum[NT / 32];
 };
@@ -405,17 +406,28 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
                 for (int l = 0; l < d; ++l) lhs += fabsf(R.r[l][ee] - w);
                 R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= alpha) ? 1 : 0;
                 R.it_w[k] = w;
+                R.it_sc[k] = ne - R.nz[ee];
             }
             __syncthreads();
         }
-        // each column: its first passing item is its highest passing slot
+        // each column: its first passing item is its highest passing slot (the
+        // last passing anchor in row order); with anchor_rule 1 the passing item
+        // of largest n_e - n_z, ties to the lower slot (items come highest first)
         int best = -1;
-        float bw = 0.0f;
+        float bw = 0.0f, bsc = 0.0f;
+        const int rule = ctx->anchor_rule;
         for (unsigned q = 0; q < nc; ++q)
             if (R.it_ok[off + q]) {
-                best = R.it_s[off + q];
-                bw = R.it_w[off + q];
-                break;
+                if (rule == 0) {
+                    best = R.it_s[off + q];
+                    bw = R.it_w[off + q];
+                    break;
+                }
+                if (best < 0 || R.it_sc[off + q] >= bsc) {
+                    best = R.it_s[off + q];
+                    bw = R.it_w[off + q];
+                    bsc = R.it_sc[off + q];
+                }
             }
         const bool pass = best >= 0;
         float nv = old;

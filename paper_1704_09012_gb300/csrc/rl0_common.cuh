@@ -123,6 +123,7 @@ struct DecodeCtx {
     float conv_tol;           // Alg. 1: converged when every |r_i| <= conv_tol (0: Alg. 2's stop level)
     int wait_test;            // 0: the column kernel's first bounded wait makes its built-in number
     unsigned wait_polls;      // of polls; 1: it makes wait_polls (rl0_expander_set_wait_polls)
+    int anchor_rule;          // 0: a column takes its last passing anchor; 1: the largest n_e - n_z
 };
 
 struct UndoEntry {

@@ -257,7 +257,7 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
         S.c.rhs[tid] = rhs;
     }
     int best = -1;
-    float bw = 0.0f;
+    float bw = 0.0f, bsc = 0.0f;
     while (__syncthreads_or(cand != 0u)) {
         int my = -1, ms = 0;
         if (cand) {
@@ -324,10 +324,16 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
             }
         }
         __syncthreads();
-        if (my >= 0 && S.c.ok[my]) {                // the first pass from the top is the last passing
-            best = ms;                              // anchor in row order: it stands, the rest is moot
-            bw = S.c.w[my];
-            cand = 0u;
+        if (my >= 0 && S.c.ok[my]) {
+            if (ctx->anchor_rule == 0) {            // the first pass from the top is the last passing
+                best = ms;                          // anchor in row order: it stands, the rest is moot
+                bw = S.c.w[my];
+                cand = 0u;
+            } else if (best < 0 || S.c.score[my] >= bsc) {   // largest n_e - n_z; slots come highest
+                best = ms;                                   // first, so >= leaves ties to the lower row
+                bw = S.c.w[my];
+                bsc = S.c.score[my];
+            }
         }
         if (tid == 0) S.nq = 0;
     }
@@ -879,7 +885,8 @@ static bool same_params(const rl0_params &a, const rl0_params &b)
 {
     return a.sigma_s == b.sigma_s && a.sigma_n == b.sigma_n && a.quantised == b.quantised && a.c == b.c &&
            a.alpha == b.alpha && a.ell == b.ell && a.scorer == b.scorer && a.mlp == b.mlp &&
-           a.mlp_threshold == b.mlp_threshold && a.max_rounds == b.max_rounds && a.noiseless_tol == b.noiseless_tol;
+           a.mlp_threshold == b.mlp_threshold && a.max_rounds == b.max_rounds && a.noiseless_tol == b.noiseless_tol &&
+           a.anchor_rule == b.anchor_rule;
 }
 
 static void cached_tables(rl0_expander *A, int64_t k, const Resolved &R, DecodeCtx *ctx, RoundThr *thr)
@@ -1492,7 +1499,7 @@ extern "C" int rl0_decode_static(const rl0_expander *Ac, const float *y_dev, int
     Resolved R;
     rc = rl0::resolve(A->n, A->m, A->d, k, params, &R);
     if (rc) return rc;
-    if (R.p.adaptive_k) return RL0_ERR_UNSUPPORTED;
+    if (R.p.adaptive_k || R.p.anchor_rule != 0) return RL0_ERR_UNSUPPORTED;
     unsigned char *base = nullptr;
     rc = static_scratch_base(A->device, &base);
     if (rc) return rc;

@@ -231,6 +231,8 @@ int resolve(int64_t n, int64_t m, int d, int64_t k, const rl0_params *in, Resolv
     if (p.scorer == 1 && (!p.mlp || !(p.sigma_n > 0.0) || d > 16)) return RL0_ERR_INVALID_ARG;
     if (p.scorer == 1 && !(p.mlp_threshold >= 0.0 && p.mlp_threshold < 1.0)) return RL0_ERR_INVALID_ARG;
     if (p.profile != 0 && p.profile != 1) return RL0_ERR_INVALID_ARG;
+    if (p.anchor_rule != 0 && p.anchor_rule != 1) return RL0_ERR_INVALID_ARG;
+    if (p.anchor_rule == 1 && p.scorer == 1) return RL0_ERR_UNSUPPORTED;
     // reading: t_r = 1 - r c for every r >= 0 with t_r > 0 (counted with a
     // tolerance so that c = 0.025 gives exactly 40 rounds)
     int nr = (int)std::ceil(1.0 / p.c - 1e-9);
@@ -265,6 +267,7 @@ void fill_tables(int64_t m, int d, int64_t k, const Resolved &R, DecodeCtx *ctx,
     ctx->stop_level = R.stop_level;
     ctx->stop_rel = R.stop_rel;
     ctx->scorer = p.scorer;
+    ctx->anchor_rule = p.anchor_rule;
     ctx->mlp = p.mlp;
     const double th = (p.mlp_threshold == 0.0) ? 0.5 : p.mlp_threshold;
     ctx->mlp_threshold = (float)th;

@@ -61,7 +61,7 @@ def fit_logistic(rhos, recovered, problems):
 
 
 def cell(delta, sigma, n, d=7, problems=10, rho_step=0.01, rho_max=0.5, adaptive=False, quantised=False,
-         seed=0, out=None):
+         seed=0, out=None, alpha=0.0, anchor_rule=0, rho_start=None):
     """Sweep rho for one (delta, sigma, n) cell.  Returns the per-rho rows and rho*."""
     import torch
     import gm
@@ -70,8 +70,9 @@ def cell(delta, sigma, n, d=7, problems=10, rho_step=0.01, rho_max=0.5, adaptive
     rows = []
     rho_star = 0.0
     steps = int(round(rho_max / rho_step))
+    first = 1 if rho_start is None else max(1, int(round(rho_start / rho_step)))
     A = None
-    for step in range(1, steps + 1):
+    for step in range(first, steps + 1):
         rho = round(step * rho_step, 10)
         k = max(1, int(rho * m))
         ok, times, rounds = 0, [], []
@@ -82,7 +83,8 @@ def cell(delta, sigma, n, d=7, problems=10, rho_step=0.01, rho_max=0.5, adaptive
             A = rl0.Expander.random(n, m, d, seed=s)
             x, _ = gm.draw_signal(n, k, 1.0, s)
             y = rl0.sketch(A, torch.from_numpy(x).cuda(), sigma_n=sigma, noise_seed=s + 7)
-            xh, st = rl0.decode(A, y, k, sigma_n=sigma, adaptive_k=adaptive, quantised=quantised)
+            xh, st = rl0.decode(A, y, k, sigma_n=sigma, adaptive_k=adaptive, quantised=quantised, alpha=alpha,
+                                anchor_rule=anchor_rule)
             if success(xh.cpu().numpy().astype(np.float64), x.astype(np.float64), m, sigma):
                 ok += 1
                 times.append(st["ms"])
@@ -91,7 +93,7 @@ def cell(delta, sigma, n, d=7, problems=10, rho_step=0.01, rho_max=0.5, adaptive
                "recovered": ok, "problems": problems,
                "ms_recovered_mean": float(np.mean(times)) if times else None,
                "rounds_recovered_mean": float(np.mean(rounds)) if rounds else None,
-               "adaptive_k": int(adaptive), "quantised": int(quantised)}
+               "adaptive_k": int(adaptive), "quantised": int(quantised), "alpha": alpha, "anchor_rule": anchor_rule}
         rows.append(row)
         if out is not None:
             print(json.dumps(row), file=out, flush=True)
@@ -116,12 +118,17 @@ def main(argv=None):
     ap.add_argument("--adaptive", action="store_true")
     ap.add_argument("--quantised", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--alpha", type=float, default=0.0, help="consensus threshold (0: the default reading)")
+    ap.add_argument("--anchor-rule", type=int, default=0, help="0: last passing anchor; 1: largest n_e - n_z")
+    ap.add_argument("--rho-start", type=float, default=None)
     a = ap.parse_args(argv)
     rows, rho_star = cell(a.delta, a.sigma, 1 << a.log2n, a.d, a.problems, a.rho_step, a.rho_max, a.adaptive,
-                          a.quantised, a.seed, out=sys.stdout)
+                          a.quantised, a.seed, out=sys.stdout, alpha=a.alpha, anchor_rule=a.anchor_rule,
+                          rho_start=a.rho_start)
     rho50, w, width = fit_logistic([r["rho"] for r in rows], [r["recovered"] for r in rows], a.problems)
     print(json.dumps({"summary": True, "delta": a.delta, "sigma": a.sigma, "n": 1 << a.log2n,
-                      "adaptive_k": int(a.adaptive), "quantised": int(a.quantised), "rho_star": rho_star,
+                      "adaptive_k": int(a.adaptive), "quantised": int(a.quantised), "alpha": a.alpha,
+                      "anchor_rule": a.anchor_rule, "rho_star": rho_star,
                       "rho50_logistic": rho50, "width_90_10": width}), flush=True)
 
 

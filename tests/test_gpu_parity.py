@@ -318,3 +318,30 @@ def test_full_size_round_and_decode_properties(rl0):
     tol = min((I.m * I.sigma_n * math.sqrt(2 / math.pi) + math.sqrt(I.m * I.sigma_n ** 2 * (1 - 2 / math.pi))) / xl1,
               0.1)
     assert np.abs(xg - I.x).sum() / xl1 <= tol
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_largest_score_anchor_rule_matches_oracle(rl0, seed):
+    """The other reading of Alg. 2's per-anchor update (anchor_rule = 1: a column takes the
+    passing anchor of largest n_e - n_z, ties to the lower row) against the oracle's
+    best_anchor flag, quantised scores (integer n_e - n_z, so the choice is exact on both
+    sides).  The batched decoder and the static entry reject it."""
+    I, y32 = _problem(seed=seed, **gm.config_small())
+    A = rl0.Expander.from_rows(_cuda(I.rows), I.m)
+    xg, st = rl0.decode(A, _cuda(y32), I.k, sigma_n=I.sigma_n, quantised=True, anchor_rule=1)
+    xo, sto, _ = oracle.decode(I.rows, y32.astype(np.float64), I.k, sigma_n=I.sigma_n, quantised=True,
+                               best_anchor=True)
+    xg = xg.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert _rel(xg, xo) <= XTOL
+    assert st["rounds"] == sto["rounds"] and st["accepted_rounds"] == sto["accepted_rounds"]
+    # the default reading on the same expander afterwards is unaffected
+    x0, _ = rl0.decode(A, _cuda(y32), I.k, sigma_n=I.sigma_n, quantised=True)
+    xo0, _, _ = oracle.decode(I.rows, y32.astype(np.float64), I.k, sigma_n=I.sigma_n, quantised=True)
+    assert np.array_equal(np.nonzero(x0.cpu().numpy())[0], np.nonzero(xo0)[0])
+    with pytest.raises(rl0.Rl0Error) as e:
+        rl0.decode_batched([A], [_cuda(y32)], [I.k], [dict(sigma_n=I.sigma_n, anchor_rule=1)])
+    assert e.value.code == -5
+    with pytest.raises(rl0.Rl0Error) as e:
+        rl0.decode_static(A, _cuda(y32), I.k, sigma_n=I.sigma_n, anchor_rule=1)
+    assert e.value.code == -5
