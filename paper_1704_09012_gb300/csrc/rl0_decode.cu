@@ -472,6 +472,16 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rows_from_x(KArgs a)
     }
 }
 
+// p_z(r_i) of r_hat under the posteriors now in ctx (after the adaptive_k
+// step changed the prior; the rebuild stored p_z under the prior of its round).
+__global__ void k_refresh_pz(KArgs a)
+{
+    const DecodeCtx *ctx = a.ctx;
+    float2 *rz = a.st->cur ? a.rz1 : a.rz0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += gridDim.x * blockDim.x)
+        rz[i].y = ctx->indicator ? 0.0f : series_eval(ctx->pz, rz[i].x);
+}
+
 // (column, FP32 bits of x_hat) of every support entry, for the host's
 // adaptive_k step.
 __global__ void k_support_pairs(KArgs a, int *out)
@@ -1073,6 +1083,10 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
         if (!R.indicator) {
             rl0::pz_lower_bounds(A->m, A->d, k, R, H->pzlb, kprior);
             CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
+            // n_z of the next round sums p_z(r_hat) under the new prior
+            k_refresh_pz<<<2 * a.nsm, 256, 0, s>>>(a);
+            launches += 1;
+            CK(cudaGetLastError());
         }
     }
     k_final_sum<<<1, 32, 0, s>>>(a);

@@ -185,3 +185,31 @@ def _compare_decode(I, y32, xg, st, log, quantised):
     print("  n=%d m=%d k=%d: differs from round %d of %d (%d near-threshold decisions there)"
           % (I.n, I.m, I.k, rstar, len(lo), near.size))
     return 0
+
+
+def test_full_size_adaptive_decode_matches_oracle(rl0):
+    """adaptive_k on the benchmark's instance (Section "Adaptive k"): the GPU's sequence of
+    priors, accepts and updates round by round is the oracle's, and so is its outcome --
+    here both stop improving after six accepted rounds, with the prior at its floor
+    m/100, 0.1% above the stop level, and sweep to t <= 0 without converging.  (Every
+    round's n_z must use p_z under that round's prior: this test is what found p_z of
+    r_hat left at the previous prior.)"""
+    rows, x, y32, cfg = _bench_instance()
+    m, k, sn = cfg["m"], cfg["k"], cfg["sigma_n"]
+    A = rl0.Expander.from_rows(torch.from_numpy(rows).cuda(), m)
+    xg, st = rl0.decode(A, torch.from_numpy(y32).cuda(), k, sigma_n=sn, adaptive_k=True)
+    log = rl0.decode_log(A)
+    with oracle.openmp():
+        xo, so, lo = oracle.decode(rows, y32.astype(np.float64), k, sigma_n=sn, adaptive_k=True)
+    xg = xg.cpu().numpy().astype(np.float64)
+    print("\nadaptive n=2^20: rounds %d/%d accepted %d/%d converged %d/%d final_l1 %.6g/%.6g" % (
+        st["rounds"], so["rounds"], st["accepted_rounds"], so["accepted_rounds"], st["converged"], so["converged"],
+        st["final_l1"], so["final_l1"]))
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert np.linalg.norm(xg - xo) <= XTOL * np.linalg.norm(xo)
+    assert st["rounds"] == so["rounds"] and st["accepted_rounds"] == so["accepted_rounds"]
+    assert st["converged"] == so["converged"]
+    assert [(e["accepted"], e["updated"]) for e in log] == [(e["accepted"], e["updated"]) for e in lo]
+    # k0 is summed from FP32 x_hat here and from FP64 x_hat in the oracle
+    for e, f in zip(log, lo):
+        assert e["k_prior"] == pytest.approx(f["k_prior"], rel=1e-7)
