@@ -34,6 +34,7 @@
 
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
+#include "rl0_mma.cuh"
 #include "rl0_round.cuh"
 
 #define RL0_RES_CHUNK 32768u            // bytes per bulk copy
@@ -96,7 +97,7 @@ __device__ __forceinline__ bool mbar_try_wait_bounded(unsigned bar, unsigned par
 
 // Resolve scratch, laid over the code region once the stream is done: a
 // batch of NT listed columns and their candidate items (at most DMAX each).
-template <int DMAX, int NT>
+template <int DMAX, int NT, bool LEARNED = false>
 struct ResScratch {
     float r[DMAX][NT];                   // FP32 residuals of the batch's columns
     float nz[NT], rhs[NT];
@@ -106,6 +107,7 @@ struct ResScratch {
     unsigned char it_ok[NT * DMAX];
     float it_w[NT * DMAX];
     float it_sc[NT * DMAX];              // n_e - n_z of the item
+    float feat[LEARNED ? NT : 1][RL0_NFEAT];   // learned scorer: features of NT items at a time
     float q[NT][DMAX];                   // q_e of (item, slot l), NT items at a time
     unsigned wsum[NT / 32];
 };
@@ -144,7 +146,7 @@ __device__ __forceinline__ unsigned cta_exclusive_scan(unsigned v, unsigned *wsu
 // One round's column score up to the CTA's commit (load, stream, resolve).
 // DMAX slots per column; EXACT: d == DMAX (the slot guards fold away).
 // cur, round: the decode state's accepted buffer and round (read by the caller).
-template <int DMAX, bool IND, bool EXACT, int NT>
+template <int DMAX, bool IND, bool EXACT, int NT, bool LEARNED>
 __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
 {
     // exact d <= 8: two columns per thread in FP16 lanes (code_candidates2)
@@ -219,7 +221,10 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         j0 = hi;
     }
     const CodeThr ct = code_thresholds(th.ta, th.tz, IND ? th.te : S.pe.cut);
-    const float need = IND ? ctx->alpha : ctx->alpha - 1e-3f;
+    // the count the code bound must allow: Alg. 2's alpha, or the learned
+    // scorer's candidate threshold (the slack covers FP32 rounding of n_e)
+    const float need0 = LEARNED ? ctx->learned_need : ctx->alpha;
+    const float need = IND ? need0 : need0 - 1e-3f;
     int32_t *passed = ctx->passed;
     const int lane = tid & 31;
     // this CTA's survivors: the first qcap in shared memory, the others in its
@@ -322,7 +327,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();                               // the stream is done: the codes' bytes become scratch
     const int count = min(S.count, hi - lo);
-    ResScratch<DMAX, NT> &R = *(ResScratch<DMAX, NT> *)dsm;
+    ResScratch<DMAX, NT, LEARNED> &R = *(ResScratch<DMAX, NT, LEARNED> *)dsm;
     const float alpha = ctx->alpha;
     for (int b0 = 0; b0 < count; b0 += NT) {
         // one thread per listed column: FP32 residuals, exact candidates
@@ -404,11 +409,40 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
                 const float w = num / ne;
                 float lhs = 0.0f;
                 for (int l = 0; l < d; ++l) lhs += fabsf(R.r[l][ee] - w);
-                R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= alpha) ? 1 : 0;
+                if constexpr (LEARNED) {
+                    // the learned scorer: the l1 test and n_e - n_z >= 1.5 here, the
+                    // network's logit below
+                    R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= ctx->learned_need) ? 1 : 0;
+                    AnchorEval E;
+                    E.ne = ne;
+                    E.w = w;
+                    E.lhs = lhs;
+                    float f[RL0_NFEAT];
+                    candidate_features(&R.r[0][ee], NT, d, E, R.nz[ee], R.rhs[ee], ctx->inv_sn, th.t, ctx->drho, f);
+#pragma unroll
+                    for (int q = 0; q < RL0_NFEAT; ++q) R.feat[kk][q] = f[q];
+                } else {
+                    R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= alpha) ? 1 : 0;
+                }
                 R.it_w[k] = w;
                 R.it_sc[k] = ne - R.nz[ee];
             }
             __syncthreads();
+            if constexpr (LEARNED) {
+                // the items' logits, 16 per warp on the tensor cores
+                const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
+                for (unsigned t0 = (unsigned)(tid >> 5) * 16u; t0 < kn; t0 += (NT / 32) * 16u) {
+                    auto f = [&](int r, int i) { return (t0 + r < kn) ? R.feat[t0 + r][i] : 0.0f; };
+                    float lo, hi;
+                    warp_mlp_logits16(f, wb, &lo, &hi);
+                    if ((tid & 3) == 0) {
+                        const unsigned gr = (unsigned)((tid & 31) >> 2);
+                        if (t0 + gr < kn && !(lo >= ctx->logit_thr)) R.it_ok[k0 + t0 + gr] = 0;
+                        if (t0 + gr + 8 < kn && !(hi >= ctx->logit_thr)) R.it_ok[k0 + t0 + gr + 8] = 0;
+                    }
+                }
+                __syncthreads();
+            }
         }
         // each column: its first passing item is its highest passing slot (the
         // last passing anchor in row order); with anchor_rule 1 the passing item
@@ -469,11 +503,11 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     return true;
 }
 
-template <int DMAX, bool IND, bool EXACT, int NT>
+template <int DMAX, bool IND, bool EXACT, int NT, bool LEARNED>
 __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    if (!column_phase<DMAX, IND, EXACT, NT>(a, dsm)) return;     // the decode is done
+    if (!column_phase<DMAX, IND, EXACT, NT, LEARNED>(a, dsm)) return;     // the decode is done
     // the codes are no longer needed: their bytes become H_k's scratch
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
     HkShared &hk = *(HkShared *)dsm;
@@ -492,10 +526,12 @@ template <int DMAX, bool EXACT>
 bool res_attr(unsigned smem)
 {
     constexpr int NT = ResNT<DMAX, EXACT>::value;
-    if (cudaFuncSetAttribute(k_column_score_res<DMAX, false, EXACT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_column_score_res<DMAX, true, EXACT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    const int sm = (int)smem;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_column_score_res<DMAX, false, EXACT, NT, false>, at, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_column_score_res<DMAX, true, EXACT, NT, false>, at, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_column_score_res<DMAX, false, EXACT, NT, true>, at, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_column_score_res<DMAX, true, EXACT, NT, true>, at, sm) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -504,14 +540,16 @@ bool res_attr(unsigned smem)
 
 // Variant for column degree d: exact for 6 <= d <= 8, else the smallest DMAX >= d.
 int res_variant(int d) { return (d >= 6 && d <= 8) ? d : (d < 6 ? 8 : (d <= 16 ? 16 : 32)); }
+// (the learned variant's scratch, which adds the features of NT items, is the larger)
 size_t res_scratch_bytes(int d)
 {
     switch (res_variant(d)) {
-    case 6: return sizeof(ResScratch<6, ResNT<6, true>::value>);
-    case 7: return sizeof(ResScratch<7, ResNT<7, true>::value>);
-    case 8: return d == 8 ? sizeof(ResScratch<8, ResNT<8, true>::value>) : sizeof(ResScratch<8, ResNT<8, false>::value>);
-    case 16: return sizeof(ResScratch<16, ResNT<16, false>::value>);
-    default: return sizeof(ResScratch<32, ResNT<32, false>::value>);
+    case 6: return sizeof(ResScratch<6, ResNT<6, true>::value, true>);
+    case 7: return sizeof(ResScratch<7, ResNT<7, true>::value, true>);
+    case 8: return d == 8 ? sizeof(ResScratch<8, ResNT<8, true>::value, true>)
+                          : sizeof(ResScratch<8, ResNT<8, false>::value, true>);
+    case 16: return sizeof(ResScratch<16, ResNT<16, false>::value, true>);
+    default: return sizeof(ResScratch<32, ResNT<32, false>::value, true>);
     }
 }
 
@@ -564,13 +602,19 @@ void rl0_res_setup(const rl0_expander *A, KArgs *a)
     a->res_ok = 1;
 }
 
-bool rl0_res_launch(const KArgs &a, int indicator, cudaStream_t s)
+bool rl0_res_launch(const KArgs &a, int indicator, int learned, cudaStream_t s)
 {
-    if (!a.res_ok) return false;
-#define RL0_CR(D, E) do {                                                                                   \
-        constexpr int NT_ = ResNT<D, E>::value;                                                              \
-        if (indicator) launch_pdl(k_column_score_res<D, true, E, NT_>, a.res_grid, NT_, a.res_smem, s, a); \
-        else launch_pdl(k_column_score_res<D, false, E, NT_>, a.res_grid, NT_, a.res_smem, s, a);          \
+    if (!a.res_ok || (learned && a.d > 16)) return false;
+#define RL0_CR(D, E) do {                                                                                        \
+        constexpr int NT_ = ResNT<D, E>::value;                                                                   \
+        if (learned) {                                                                                            \
+            if (indicator) launch_pdl(k_column_score_res<D, true, E, NT_, true>, a.res_grid, NT_, a.res_smem, s, a); \
+            else launch_pdl(k_column_score_res<D, false, E, NT_, true>, a.res_grid, NT_, a.res_smem, s, a);      \
+        } else if (indicator) {                                                                                   \
+            launch_pdl(k_column_score_res<D, true, E, NT_, false>, a.res_grid, NT_, a.res_smem, s, a);            \
+        } else {                                                                                                  \
+            launch_pdl(k_column_score_res<D, false, E, NT_, false>, a.res_grid, NT_, a.res_smem, s, a);           \
+        }                                                                                                         \
     } while (0)
     switch (res_variant(a.d)) {
     case 6: RL0_CR(6, true); break;

@@ -31,6 +31,7 @@
 
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
+#include "rl0_mma.cuh"
 #include "rl0_round.cuh"
 #include <cuda_bf16.h>
 
@@ -194,8 +195,6 @@ struct ColShared {
             float score[NT], w[NT];
             unsigned char ok[NT];
             float f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the queued candidates
-            float h1[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];     // hidden layers of a 32-candidate slice
-            float h2[LEARNED ? RL0_HID : 1][LEARNED ? 32 : 1];
             unsigned char l1ok[LEARNED ? NT : 1];
         } c;
         struct {
@@ -204,7 +203,6 @@ struct ColShared {
         } h;
     };
     Series pe;
-    float W[LEARNED ? RL0_MLP_PARAMS : 1];     // learned scorer parameters (FP32 copies)
     int nq;
     int last;
 };
@@ -216,10 +214,6 @@ __device__ __forceinline__ void col_setup(const DecodeCtx *ctx, ColShared<DMAX, 
     if (tid == 0) {
         S.nq = 0;
         if (!IND) S.pe = ctx->pe;
-    }
-    if (LEARNED) {
-        const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
-        for (int p = tid; p < RL0_MLP_PARAMS; p += NT) S.W[p] = __bfloat162float(wb[p]);
     }
     // (these shared copies are first read after a barrier of the tile body)
 }
@@ -285,33 +279,24 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
                 S.c.w[e] = E.w;
             }
             __syncthreads();
-            for (int e0 = 0; e0 < nq; e0 += 32) {
-                for (int it = tid; it < 32 * RL0_HID; it += NT) {
-                    const int el = it % 32, o = it / 32, e = e0 + el;
-                    float acc = S.W[RL0_OFF_B1 + o];
-                    if (e < nq) {
-#pragma unroll
-                        for (int i = 0; i < RL0_NFEAT; ++i) acc = fmaf(S.c.f[i][e], S.W[RL0_OFF_W1 + i * RL0_HID + o], acc);
+            // the queued candidates' logits, 16 per warp on the tensor cores
+            // (rl0_mma.cuh: the arithmetic of rl0_mlp_forward)
+            const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
+            for (int e0 = (tid >> 5) * 16; e0 < nq; e0 += (NT / 32) * 16) {
+                auto f = [&](int r, int i) { return (e0 + r < nq) ? S.c.f[i][e0 + r] : 0.0f; };
+                float lo, hi;
+                warp_mlp_logits16(f, wb, &lo, &hi);
+                if ((tid & 3) == 0) {
+                    const int gr = (tid & 31) >> 2;
+                    if (e0 + gr < nq) {
+                        S.c.score[e0 + gr] = lo;
+                        S.c.ok[e0 + gr] = (S.c.l1ok[e0 + gr] && lo >= ctx->logit_thr) ? 1 : 0;
                     }
-                    S.c.h1[o][el] = fmaxf(acc, 0.0f);
+                    if (e0 + gr + 8 < nq) {
+                        S.c.score[e0 + gr + 8] = hi;
+                        S.c.ok[e0 + gr + 8] = (S.c.l1ok[e0 + gr + 8] && hi >= ctx->logit_thr) ? 1 : 0;
+                    }
                 }
-                __syncthreads();
-                for (int it = tid; it < 32 * RL0_HID; it += NT) {
-                    const int el = it % 32, o = it / 32;
-                    float acc = S.W[RL0_OFF_B2 + o];
-#pragma unroll 8
-                    for (int i = 0; i < RL0_HID; ++i) acc = fmaf(S.c.h1[i][el], S.W[RL0_OFF_W2 + i * RL0_HID + o], acc);
-                    S.c.h2[o][el] = fmaxf(acc, 0.0f);
-                }
-                __syncthreads();
-                if (tid < 32 && e0 + tid < nq) {
-                    const int e = e0 + tid;
-                    float out = S.W[RL0_OFF_B3];
-                    for (int o = 0; o < RL0_HID; ++o) out = fmaf(S.c.h2[o][tid], S.W[RL0_OFF_W3 + o], out);
-                    S.c.score[e] = out;
-                    S.c.ok[e] = (S.c.l1ok[e] && out >= ctx->logit_thr) ? 1 : 0;
-                }
-                __syncthreads();
             }
         } else {
             for (int e = tid; e < nq; e += NT) {
@@ -642,7 +627,7 @@ KArgs make_args(const rl0_expander *A)
 // the resident-code kernel, which also fills the rebuild's buckets.
 bool launch_column_score(const KArgs &a, int dmax, int indicator, int learned, cudaStream_t s)
 {
-    if (!learned && rl0_res_launch(a, indicator, s)) return true;
+    if (rl0_res_launch(a, indicator, learned, s)) return true;
 #define RL0_CS(D, I, L) launch_pdl(k_column_score<D, I, L>, rl0_div_up(a.n, ColBlock<D>::value), ColBlock<D>::value, 0, s, a)
     if (learned) {
         if (dmax == 8) { if (indicator) RL0_CS(8, true, true); else RL0_CS(8, false, true); }
@@ -1139,7 +1124,7 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
-    if (!R.indicator && R.p.scorer == 0) {
+    if (!R.indicator) {                           // the resident-code column kernel's n_z bound
         cached_pz(A, k, R, H->pzlb);
         CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
     }
@@ -1394,7 +1379,7 @@ extern "C" int rl0_round_step(const rl0_expander *Ac, const float *y_dev, int64_
     const Workspace &w = A->ws;
     CK(cudaMemcpyAsync(w.ctx, &H->ctx, sizeof(DecodeCtx), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
-    if (!R.indicator && R.p.scorer == 0) {
+    if (!R.indicator) {
         rl0::pz_lower_bounds(A->m, A->d, k, R, H->pzlb);
         CK(cudaMemcpyAsync(w.pzlb, H->pzlb, sizeof(H->pzlb), cudaMemcpyHostToDevice, s));
     }

@@ -2,7 +2,8 @@
 // with ReLU hidden layers and a logistic output, trained with binary
 // cross-entropy on candidate features logged from analytic Robust-l0 decodes
 // (labels: the candidate update x_j + w lands on the true x_j).  FP32 master
-// weights train here; decodes use a BF16 copy with FP32 accumulation.
+// weights train here; decodes use a BF16 copy with FP32 accumulation, on the
+// tensor cores (rl0_mma.cuh).
 //
 // The gradient is deterministic: each block of RL0_MLP_BLOCK samples writes its
 // own partial gradient (sums over its samples in index order), and a second
@@ -14,6 +15,7 @@
 
 #include "rl0_common.cuh"
 #include "rl0_device.cuh"
+#include "rl0_mma.cuh"
 
 #define CK(call)                                          \
     do {                                                  \
@@ -175,18 +177,21 @@ __global__ void k_mlp_export(const float *w, __nv_bfloat16 *wb)
     if (p < RL0_MLP_PARAMS) wb[p] = __float2bfloat16_rn(w[p]);
 }
 
-// Logits of N feature rows with the BF16 parameters (the decode's arithmetic).
-__global__ void k_mlp_forward(const __nv_bfloat16 *wb, const float *feat, long long N, float *logit)
+// Logits of N feature rows with the BF16 parameters: the decoder's arithmetic
+// (warp_mlp_logits16 on the tensor cores), one warp per 16 rows.
+__global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16 *wb, const float *feat, long long N,
+                                                      float *logit)
 {
-    __shared__ float W[RL0_MLP_PARAMS];
-    for (int p = threadIdx.x; p < RL0_MLP_PARAMS; p += blockDim.x) W[p] = __bfloat162float(wb[p]);
-    __syncthreads();
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    float f[RL0_NFEAT];
-#pragma unroll
-    for (int i = 0; i < RL0_NFEAT; ++i) f[i] = feat[s * RL0_NFEAT + i];
-    logit[s] = mlp_logit(W, f);
+    const long long r0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32 * 16;
+    if (r0 >= N) return;                           // whole warps leave together
+    auto f = [&](int r, int i) { return (r0 + r < N) ? feat[(r0 + r) * RL0_NFEAT + i] : 0.0f; };
+    float lo, hi;
+    warp_mlp_logits16(f, wb, &lo, &hi);
+    const int g = (threadIdx.x & 31) >> 2;
+    if ((threadIdx.x & 3) == 0) {
+        if (r0 + g < N) logit[r0 + g] = lo;
+        if (r0 + g + 8 < N) logit[r0 + g + 8] = hi;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -307,7 +312,8 @@ extern "C" int rl0_mlp_forward(const void *wbf16_dev, const float *feat_dev, int
 {
     if (!wbf16_dev || !feat_dev || !logit_dev || N < 0) return RL0_ERR_INVALID_ARG;
     if (N == 0) return RL0_OK;
-    k_mlp_forward<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+    // 16 rows per warp, 8 warps per block
+    k_mlp_forward<<<(unsigned)((N + 127) / 128), 256, 0, (cudaStream_t)cuda_stream>>>(
         (const __nv_bfloat16 *)wbf16_dev, feat_dev, N, logit_dev);
     CK(cudaGetLastError());
     return RL0_OK;

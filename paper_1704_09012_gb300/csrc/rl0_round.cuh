@@ -489,8 +489,8 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
 // Column kernel with every row's residual code in shared memory
 // (rl0_column_res.cu).  rl0_res_setup fills a's res_* fields for expander A
 // (res_ok = 0 when the codes do not fit the device's shared memory or the
-// workspace has no code buffers); rl0_res_launch launches it and returns false
-// when a.res_ok is 0.
+// workspace has no code buffers); rl0_res_launch launches it (the learned
+// scorer's variant when learned is set) and returns false when a.res_ok is 0.
 void rl0_res_setup(const rl0_expander *A, KArgs *a);
 int rl0_res_dmax(int d);                     // slots per survivor-list entry for degree d
-bool rl0_res_launch(const KArgs &a, int indicator, cudaStream_t s);
+bool rl0_res_launch(const KArgs &a, int indicator, int learned, cudaStream_t s);
