@@ -280,13 +280,32 @@ int rl0_decode_log(const rl0_expander *A, rl0_round_record *out, int cap);
 /* Features of every learned-scorer candidate of one round from an injected state
  * (x_hat, r_hat: device, n and m floats) at t = 1 - round_index c: feat_dev
  * (cap x 16 floats), meta_dev (cap x 4 int32: column, slot, passes the analytic test,
- * passes the l1 test), omega_dev (cap floats: the consensus value w).  *count_out
- * (host) receives the number of candidates (only min(count, cap) are written).
+ * passes the l1 test), omega_dev (cap floats: the consensus value w), in ascending
+ * (column, slot) order.  *count_out (host) receives the number of candidates (only
+ * min(count, cap) are written).
  * Requires sigma_n > 0 and d <= 16. */
 int rl0_candidate_features(const rl0_expander *A, const float *y_dev, int64_t k,
                            const rl0_params *params, int round_index, const float *xhat_dev,
                            const float *rhat_dev, float *feat_dev, int32_t *meta_dev,
                            float *omega_dev, int cap, int *count_out, void *cuda_stream);
+
+/* Training data for the scorer: runs Algorithm 2 with the analytic rule (params->scorer
+ * must be 0, adaptive_k 0; sigma_n > 0) from x_hat = 0, r_hat = y, for rounds
+ * 1 .. max_rounds - 1, each as rl0_round_step computes it, keeping the round's candidate
+ * when ||r||_1 < ||r_hat||_1 and stopping once ||r_hat||_1 <= m sigma_n sqrt(2/pi) (the
+ * expected l1 norm of the noise, Section 'Stopping conditions').  Before each round the
+ * features of every candidate of that round (as rl0_candidate_features gives them, in
+ * ascending (column, slot) order) are appended to feat_dev (rows of 16 floats), with
+ * label_dev = 1 when x_hat_j + w lies within tol_sigma sigma_n of x_true_j != 0
+ * (xtrue_dev: device, n floats), else 0.  At most cap rows are written (feat_dev and
+ * label_dev may be NULL when cap = 0); *count_out (host) receives the number of
+ * candidates met, which may exceed cap; *rounds_out (host, may be NULL) the rounds run.
+ * Allocates its scratch per call; synchronises the stream.  2 <= max_rounds <= 1024,
+ * tol_sigma > 0. */
+int rl0_scorer_log(const rl0_expander *A, const float *y_dev, int64_t k, const rl0_params *params,
+                   const float *xtrue_dev, float tol_sigma, int max_rounds, float *feat_dev,
+                   float *label_dev, int64_t cap, int64_t *count_out, int *rounds_out,
+                   void *cuda_stream);
 
 /* FP32 parameters, He-normal weights and zero biases from a counter-based hash of seed. */
 int rl0_mlp_init(uint64_t seed, float *w_dev, void *cuda_stream);

@@ -33,7 +33,7 @@ EXPORTS = [
     "rl0_decode_batched", "rl0_decode_log", "rl0_strerror", "rl0_decode_static", "rl0_expander_set_wait_polls",
     "rl0_parallel_l0",
     "rl0_posterior_mc",
-    "rl0_candidate_features", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
+    "rl0_candidate_features", "rl0_scorer_log", "rl0_mlp_init", "rl0_mlp_grad", "rl0_mlp_train", "rl0_mlp_export",
     "rl0_mlp_forward", "rl0_mlp_params",
 ]
 MLP_PARAMS = 1633
@@ -107,6 +107,8 @@ def _lib():
                                        vp, vp, vp]
         L.rl0_candidate_features.argtypes = [vp, vp, i64, C.POINTER(Params), i32, vp, vp, vp, vp, vp, i32,
                                              C.POINTER(i32), vp]
+        L.rl0_scorer_log.argtypes = [vp, vp, i64, C.POINTER(Params), vp, C.c_float, i32, vp, vp, i64,
+                                     C.POINTER(i64), C.POINTER(i32), vp]
         L.rl0_mlp_init.argtypes = [C.c_uint64, vp, vp]
         L.rl0_mlp_grad.argtypes = [vp, vp, vp, i64, vp, C.POINTER(C.c_double), vp]
         L.rl0_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, vp, C.POINTER(C.c_double), vp]
@@ -359,6 +361,27 @@ def candidate_features(A, y, k, round_index, xhat, rhat, cap=None, stream=None, 
                                          C.byref(cnt), _stream(stream)), "rl0_candidate_features")
     c = min(cnt.value, cap)
     return feat[:c], meta[:c], omega[:c]
+
+
+def scorer_log(A, y, k, x_true, max_rounds=40, tol_sigma=4.0, cap=None, stream=None, **params):
+    """Labelled candidates of an analytic decode of (A, y), for training the scorer
+    (rl0_scorer_log).  x_true: CUDA float32 [n].  Returns (features [N, 16], labels [N],
+    rounds run), CUDA tensors."""
+    p = make_params(**params)
+    if cap is None:
+        cap = 8 * A.n
+    xt = _dev(x_true, torch.float32, A.n, "x_true")
+    yd = _dev(y, torch.float32, A.m, "y")
+    while True:
+        feat = torch.empty((max(cap, 1), NFEAT), dtype=torch.float32, device="cuda")
+        lab = torch.empty(max(cap, 1), dtype=torch.float32, device="cuda")
+        cnt, rounds = C.c_int64(), C.c_int32()
+        _check(_lib().rl0_scorer_log(A.handle, yd, int(k), C.byref(p), xt, float(tol_sigma), int(max_rounds),
+                                     C.c_void_p(feat.data_ptr()), C.c_void_p(lab.data_ptr()), int(cap),
+                                     C.byref(cnt), C.byref(rounds), _stream(stream)), "rl0_scorer_log")
+        if cnt.value <= cap:
+            return feat[:cnt.value], lab[:cnt.value], rounds.value
+        cap = cnt.value                        # the log is deterministic: run again with room for all
 
 
 def mlp_init(seed=0, stream=None):

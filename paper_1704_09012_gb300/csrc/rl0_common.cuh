@@ -138,7 +138,7 @@ struct Workspace {
     float *pzlb;              // p_z lower bound per code bin, float[RL0_PZ_BINS]
     int *res_list;            // survivors of the column kernel's code bound, n entries of rl0_res_dmax + 2 ints
     int *list;                // support + new nonzeros, capacity n
-    int *list_tmp;            // compaction scratch, capacity n
+    int *list_tmp;            // one int: a counter
     UndoEntry *ulog;          // updates of this round, capacity n
     UndoEntry *dlog;          // H_k drops of this round, capacity n
     int *bcnt;                // per-row fresh-bucket counts, int[m] (kept zero between rounds)

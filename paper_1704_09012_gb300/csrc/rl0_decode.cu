@@ -481,31 +481,36 @@ __global__ void k_support_pairs(KArgs a, int *out)
 }
 
 // Features of every learned-scorer candidate of one round (for training logs):
-// feat[e*16..], meta[e*4..] = (column, slot, analytic pass, l1 test), omega[e].
+// feat[e*16..], meta[e*4..] = (column, slot, analytic pass, l1 test), omega[e],
+// in ascending (column, slot) order.  Two passes over the same arithmetic:
+// pass 0 writes each block's candidate count to bbase[block]; k_collect_scan
+// turns the counts into block offsets; pass 1 writes each candidate at its
+// block's offset plus its rank within the block.
 template <int DMAX, bool IND>
 __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_collect(KArgs a, float *feat, int *meta, float *omega,
-                                                                   int cap, int *count)
+                                                                   int cap, int *bbase, int pass)
 {
     constexpr int NT = ColBlock<DMAX>::value;
     __shared__ Series s_pe;
     __shared__ float s_r[DMAX][NT];
+    __shared__ int s_wsum[NT / 32];
     const DecodeState *st = a.st;
     const DecodeCtx *ctx = a.ctx;
     const float2 *__restrict__ rz = st->cur ? a.rz1 : a.rz0;
     const RoundThr th = a.thr[st->round];
     const float alpha = ctx->alpha;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0 && !IND) s_pe = ctx->pe;
     __syncthreads();
     const int n = a.n, d = a.d;
     const int j = blockIdx.x * NT + tid;
-    if (j >= n) return;
+    const bool active = j < n;
     float r[DMAX];
     float nz = 0.0f, rhs = 0.0f;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
         r[s] = 0.0f;
-        if (s < d) {
+        if (s < d && active) {
             const float2 v = rz[a.rows_sm[(size_t)s * n + j]];
             r[s] = v.x;
             nz += IND ? (fabsf(v.x) <= th.tz ? 1.0f : 0.0f) : v.y;
@@ -513,17 +518,43 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_collect(KArgs a, floa
         }
     }
     const float need = IND ? ctx->learned_need : ctx->learned_need - 1e-3f;
-    unsigned cand = anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, ctx->pe_b1, ctx->pe_c1, nz, need);
+    const unsigned cand0 = active ? anchor_candidates<DMAX, IND>(r, d, th.ta, IND ? th.te : s_pe.cut, ctx->pe_b1,
+                                                                 ctx->pe_c1, nz, need) : 0u;
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) s_r[s][tid] = r[s];
-    for (; cand; cand &= cand - 1u) {
+    // this column's candidates (slots in ascending order)
+    unsigned keep = 0u;
+    for (unsigned cand = cand0; cand; cand &= cand - 1u) {
         const int s = __ffs(cand) - 1;
         const AnchorEval E = eval_anchor<IND>(&s_r[0][tid], NT, d, s, th.te, s_pe);
-        if (!(E.ne - nz >= ctx->learned_need)) continue;
+        if (E.ne - nz >= ctx->learned_need) keep |= 1u << s;
+    }
+    const int c = __popc(keep);
+    // exclusive scan of c over the block
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+        if (w < wid) wbase += s_wsum[w];
+        total += s_wsum[w];
+    }
+    if (pass == 0) {
+        if (tid == 0) bbase[blockIdx.x] = total;
+        return;
+    }
+    int e = bbase[blockIdx.x] + wbase + incl - c;
+    for (; keep; keep &= keep - 1u, ++e) {
+        const int s = __ffs(keep) - 1;
+        if (e >= cap) break;
+        const AnchorEval E = eval_anchor<IND>(&s_r[0][tid], NT, d, s, th.te, s_pe);
         float f[RL0_NFEAT];
         candidate_features(&s_r[0][tid], NT, d, E, nz, rhs, ctx->inv_sn, th.t, ctx->drho, f);
-        const int e = atomicAdd(count, 1);
-        if (e >= cap) continue;
 #pragma unroll
         for (int q = 0; q < RL0_NFEAT; ++q) feat[(long long)e * RL0_NFEAT + q] = f[q];
         meta[4 * e + 0] = j;
@@ -532,6 +563,32 @@ __global__ void __launch_bounds__(ColBlock<DMAX>::value) k_collect(KArgs a, floa
         meta[4 * e + 3] = (E.lhs <= rhs) ? 1 : 0;
         omega[e] = E.w;
     }
+}
+
+// Exclusive scan of the nb block counts in place (one block); *total gets the sum.
+__global__ void __launch_bounds__(1024) k_collect_scan(int *bbase, int nb, int *total)
+{
+    __shared__ int s_part[1024];
+    const int t = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    int sum = 0;
+    for (int b = b0; b < b1; ++b) sum += bbase[b];
+    s_part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {           // Hillis-Steele inclusive scan of the parts
+        const int u = (t >= o) ? s_part[t - o] : 0;
+        __syncthreads();
+        s_part[t] += u;
+        __syncthreads();
+    }
+    int run = s_part[t] - sum;
+    for (int b = b0; b < b1; ++b) {
+        const int v = bbase[b];
+        bbase[b] = run;
+        run += v;
+    }
+    if (t == 1023) *total = s_part[1023];
 }
 
 // round_step output: the candidate residual (or r_hat when nothing changed).
@@ -1616,16 +1673,22 @@ extern "C" int rl0_candidate_features(const rl0_expander *Ac, const float *y_dev
     CK(cudaMemcpyAsync(w.thr, H->thr, R.nrounds * sizeof(RoundThr), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(w.st, 0, sizeof(DecodeState), s));
     int *cnt = (int *)w.list_tmp;
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    int *bbase = w.res_list;                       // free outside the column kernel; capacity >= n
     const KArgs a = make_args(A);
     k_rows_from<<<a.nchunks, RL0_ROWS_CHUNK, 0, s>>>(a, rhat_dev, 0, 0);
     k_start<<<1, 32, 0, s>>>(a, round_index, 0);
-    if (A->d <= 8) {
-        if (R.indicator) k_collect<8, true><<<rl0_div_up(a.n, 256), 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
-        else k_collect<8, false><<<rl0_div_up(a.n, 256), 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
-    } else {
-        if (R.indicator) k_collect<16, true><<<rl0_div_up(a.n, 128), 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
-        else k_collect<16, false><<<rl0_div_up(a.n, 128), 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, cnt);
+    for (int pass = 0; pass < 2; ++pass) {
+        if (A->d <= 8) {
+            const unsigned nb = rl0_div_up(a.n, 256);
+            if (R.indicator) k_collect<8, true><<<nb, 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, bbase, pass);
+            else k_collect<8, false><<<nb, 256, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, bbase, pass);
+            if (pass == 0) k_collect_scan<<<1, 1024, 0, s>>>(bbase, (int)nb, cnt);
+        } else {
+            const unsigned nb = rl0_div_up(a.n, 128);
+            if (R.indicator) k_collect<16, true><<<nb, 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, bbase, pass);
+            else k_collect<16, false><<<nb, 128, 0, s>>>(a, feat_dev, meta_dev, omega_dev, cap, bbase, pass);
+            if (pass == 0) k_collect_scan<<<1, 1024, 0, s>>>(bbase, (int)nb, cnt);
+        }
     }
     CK(cudaGetLastError());
     int c = 0;

@@ -73,6 +73,52 @@ __device__ __forceinline__ void b_frag_bf16(const __nv_bfloat16 *W, int ldw, int
     b[1] = bf16x2_bits(W[(k0 + 2 * q + 8) * ldw + n0 + g], W[(k0 + 2 * q + 9) * ldw + n0 + g]);
 }
 
+// A fragments (three parts) of a 16 x 16 FP32 tile whose entry (r, c) is e(r, c).
+template <class Fn>
+__device__ __forceinline__ void a_frag_split3_fn(Fn e, unsigned a[3][4])
+{
+    const int g = (threadIdx.x & 31) >> 2, q = threadIdx.x & 3;
+    float v[8];
+    v[0] = e(g, 2 * q);
+    v[1] = e(g, 2 * q + 1);
+    v[2] = e(g + 8, 2 * q);
+    v[3] = e(g + 8, 2 * q + 1);
+    v[4] = e(g, 2 * q + 8);
+    v[5] = e(g, 2 * q + 9);
+    v[6] = e(g + 8, 2 * q + 8);
+    v[7] = e(g + 8, 2 * q + 9);
+    a_frag_split3(v, a);
+}
+
+// B fragments (three parts) of a 16 x 8 FP32 tile whose entry (k, n) is e(k, n).
+template <class Fn>
+__device__ __forceinline__ void b_frag_split3_fn(Fn e, unsigned b[3][2])
+{
+    const int g = (threadIdx.x & 31) >> 2, q = threadIdx.x & 3;
+    __nv_bfloat16 p[4][3];
+    split3(e(2 * q, g), p[0]);
+    split3(e(2 * q + 1, g), p[1]);
+    split3(e(2 * q + 8, g), p[2]);
+    split3(e(2 * q + 9, g), p[3]);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        b[s][0] = bf16x2_bits(p[0][s], p[1][s]);
+        b[s][1] = bf16x2_bits(p[2][s], p[3][s]);
+    }
+}
+
+// d += a . b for two FP32 operands in three BF16 parts each: the six part
+// products whose ranks add up to at most 4, smallest first.
+__device__ __forceinline__ void mma_split3x3(float *d, const unsigned a[3][4], const unsigned b[3][2])
+{
+    mma_bf16_16816(d, a[2], b[0]);
+    mma_bf16_16816(d, a[1], b[1]);
+    mma_bf16_16816(d, a[0], b[2]);
+    mma_bf16_16816(d, a[1], b[0]);
+    mma_bf16_16816(d, a[0], b[1]);
+    mma_bf16_16816(d, a[0], b[0]);
+}
+
 // Logits of 16 rows with the BF16 parameters wb (layout of rl0.h: W1 16x32
 // input-major, b1, W2 32x32, b2, w3, b3).  f(r, i) gives feature i of row r
 // (rows 0..15 of this warp's tile).  Every lane of the warp calls it; lane

@@ -136,6 +136,42 @@ def _shape(rng, n, d):
     return m, k, sn
 
 
+def test_scorer_log_equals_the_round_loop_composed_from_round_steps(rl0):
+    """rl0_scorer_log against the same loop written here from library round steps: the
+    accept test ||r||_1 < ||r_hat||_1, the stop level m sigma_n sqrt(2/pi), and the label
+    |x_hat_j + w - x_j| <= 4 sigma_n with x_j != 0."""
+    rng = np.random.default_rng(21)
+    n, d = 1 << 13, 7
+    m, k, sn = _shape(rng, n, d)
+    I, y32 = _problem(n, m, k, d, sn, 4242)
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), m)
+    y = torch.from_numpy(y32).cuda()
+    xt = torch.from_numpy(I.x.astype(np.float32)).cuda()
+    F, Y, rounds = rl0.scorer_log(A, y, k, xt, sigma_n=sn)
+    xh = torch.zeros(n, dtype=torch.float32, device="cuda")
+    rh = y.clone()
+    l1h = float(np.abs(y32.astype(np.float64)).sum())
+    feats, labels, ran = [], [], 0
+    for r in range(1, 40):
+        f, meta, w = rl0.candidate_features(A, y, k, r, xh, rh, sigma_n=sn)
+        j = meta[:, 0].long()
+        feats.append(f.clone())
+        labels.append((((xh[j] + w) - xt[j]).abs() <= np.float32(4.0 * sn)) & (xt[j] != 0))
+        xp, rp, _, l1 = rl0.round_step(A, y, k, r, xh, rh, want_passed=False, sigma_n=sn)
+        ran += 1
+        if l1 < l1h:
+            xh, rh, l1h = xp, rp, l1
+        if l1h <= m * sn * math.sqrt(2 / math.pi):
+            break
+    Fr, Yr = torch.cat(feats), torch.cat(labels).float()
+    assert rounds == ran and F.shape == Fr.shape and F.shape[0] > 1000
+    assert torch.equal(F, Fr) and torch.equal(Y, Yr)
+    assert 0.05 < float(Y.mean()) < 0.95
+    # a capacity below the count: the binding runs again with room for all and gets the same rows
+    F2, Y2, _ = rl0.scorer_log(A, y, k, xt, cap=100, sigma_n=sn)
+    assert torch.equal(F2, F) and torch.equal(Y2, Y)
+
+
 @pytest.fixture(scope="module")
 def trained(rl0):
     """A scorer trained on the decode logs of 12 analytic decodes (n = 2^14, d = 7,
