@@ -26,7 +26,8 @@
 //            (the last passing anchor in row order); the CTA then commits with
 //            one global atomic per counter, and the columns that became
 //            nonzero go into the rebuild's fresh row buckets;
-//   H_k      the launch's last CTA (an acquire-release ticket) applies H_k
+//   H_k      the launch's last CTA (a 64-bit acquire-release ticket that also
+//            sums the CTAs' changes of the nonzero count) applies H_k
 //            when |supp x'| > k, its scratch in the bytes that held the codes.
 // The resolve runs the arithmetic of k_column_score in the same order, so
 // both kernels give the same x'.
@@ -48,18 +49,24 @@ struct ResShared {
     unsigned long long bar;             // completion of the bulk copies
     int count, last;
     unsigned total, ubase, fbase;
+    int dn;                             // this CTA's change of the nonzero count
+    unsigned nnz0;                      // |supp x_hat| at the round's start
 };
 
-// A survivor staged in shared memory: its column, candidate slots, x_j and
-// the (r, p_z) of its rows, the last two copied with cp.async.
+// A survivor staged in shared memory: its column, candidate slots, x_j, the
+// (r, p_z) of its rows (x_j and (r, p_z) copied with cp.async) and its row ids
+// (for the fresh-bucket insert if it becomes nonzero).
 template <int DMAX>
 struct ResEntry {
     int j;
     unsigned mask;
     float old, pad;
     float2 rz[DMAX];
+    int rid[DMAX + (DMAX & 1)];
 };
-static_assert(sizeof(ResEntry<7>) == 16 + 8 * 7 && sizeof(ResEntry<32>) == 16 + 8 * 32, "entry layout");
+__host__ __device__ constexpr unsigned res_entry_bytes(int d) { return 16u + 8u * d + 4u * (d + (d & 1)); }
+static_assert(sizeof(ResEntry<7>) == res_entry_bytes(7) && sizeof(ResEntry<32>) == res_entry_bytes(32),
+              "entry layout");
 
 __device__ __forceinline__ void cp_async_4(void *dst, const void *src)
 {
@@ -174,6 +181,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     pdl_wait();                                    // the previous rebuild's r, codes, x and state
     // done, cur and round in one L2 trip (the code copy waits on cur)
     const int done = st->done, cur = st->cur, round = st->round;
+    const unsigned nnz0 = st->nnz;
     pdl_launch_dependents();
     if (done) return false;
     const float2 *__restrict__ rz = cur ? a.rz1 : a.rz0;
@@ -181,6 +189,8 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&S.bar);
     if (tid == 0) {
         S.count = 0;
+        S.dn = 0;
+        S.nnz0 = nnz0;
         if (!IND) S.pe = ctx->pe;
         const unsigned code_bytes = 2u * (unsigned)rl0_code_rows(a.m);
         const unsigned bytes = code_bytes + (IND ? 0u : 4u * RL0_PZ_BINS);
@@ -242,7 +252,10 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
             cp_async_4(&q.old, xg + j);
 #pragma unroll
             for (int s = 0; s < DMAX; ++s)
-                if (s < d) cp_async_8(&q.rz[s], rz + rid[s]);
+                if (s < d) {
+                    cp_async_8(&q.rz[s], rz + rid[s]);
+                    q.rid[s] = rid[s];
+                }
         } else if (pos < hi - lo) {                 // pos < hi - lo always: one entry per column
             int *ent = seg + (size_t)pos * (DMAX + 2);
             ent[0] = j;
@@ -478,7 +491,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         const int ngone = __syncthreads_count(pass && old != 0.0f && nv == 0.0f);
         if (tid == 0) {
             const int nup = (int)(tpf & 0xffffu);
-            if (nup != ngone) atomicAdd(&st->nnz_delta, nup - ngone);
+            S.dn += nup - ngone;                   // added to the ticket at the end
             if (ngone) atomicAdd(&st->zeroed, (unsigned)ngone);
             const unsigned long long old2 = (tpf != 0u) ? take_upd_list(st, tpf >> 16, tpf & 0xffffu) : 0ull;
             S.ubase = (unsigned)(old2 >> 32);
@@ -494,8 +507,14 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         if (fresh) {
             a.list[S.fbase + (pf & 0xffffu)] = j;
             int rid[DMAX];
+            if (e < qcap) {
 #pragma unroll
-            for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? __ldg(a.rows_sm + (size_t)s2 * n + j) : 0;
+                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? sq[e].rid[s2] : 0;
+            } else {
+                const int *ent = seg + (size_t)e * (DMAX + 2);
+#pragma unroll
+                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? __ldcg(ent + 2 + s2) : 0;
+            }
             bucket_column<DMAX>(a, j, rid, d);
         }
         __syncthreads();                           // the scratch is reused by the next batch
@@ -512,7 +531,7 @@ __global__ void __launch_bounds__(NT, 1) k_column_score_res(KArgs a)
     ResShared &S = *(ResShared *)(dsm + a.res_s_off);
     HkShared &hk = *(HkShared *)dsm;
     unsigned *suf = (unsigned *)(dsm + ((sizeof(HkShared) + 15) & ~(size_t)15));
-    last_cta_hk<NT>(a, a.ctx, hk, suf, &S.last);
+    last_cta_hk_tick<NT>(a, a.ctx, hk, suf, &S.last, S.dn, S.nnz0);
 }
 
 // Threads per CTA of each variant: 512 up to 16 slots (the paired exact
@@ -585,7 +604,7 @@ void rl0_res_setup(const rl0_expander *A, KArgs *a)
     if (a->res_q_off > (unsigned)optin) return;
     // the shared memory left over stages survivors (one CTA per SM: nothing
     // else competes for it); the others go to the global list
-    const unsigned eb = 16u + 8u * (unsigned)res_variant(A->d);
+    const unsigned eb = res_entry_bytes(res_variant(A->d));
     a->res_qcap = (int)std::min<unsigned>(((unsigned)optin - a->res_q_off) / eb, 4096u);
     a->res_smem = a->res_q_off + (unsigned)a->res_qcap * eb;
     bool ok = false;

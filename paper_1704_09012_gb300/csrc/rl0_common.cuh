@@ -88,6 +88,8 @@ struct DecodeState {
     int accepted_rounds;
     int hk_rounds;
     int fallback_rounds;
+    unsigned long long tick;  // resident-code column kernel: CTAs done (bits 48..63) and their
+                              // changes of the nonzero count, each biased by 2^31 (bits 0..47)
     double l1_hat;
     double l1_new;
     double final_l1;          // ||y_hat - A x_hat||_1 in FP64 (epilogue)

@@ -121,6 +121,7 @@ __global__ void k_start(KArgs a, int round0, int empty_support)
     st->done = (status != 0) || st->converged || (round0 >= a.ctx->nrounds);
     st->nnz = st->shat_count;
     st->nnz_delta = 0;
+    st->tick = 0ull;
     st->zeroed = 0;
     st->iters = 0;
     st->skipped = 0;

@@ -184,6 +184,45 @@ __device__ __forceinline__ void last_cta_hk(const KArgs &a, const DecodeCtx *ctx
     cta_hk_select<NT>(a.list, __ldcg(&stw->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &stw->drop_count, hk, suf);
 }
 
+// The resident-code kernel's ticket: one acquire-release atomic per CTA adds 1
+// to the CTA count (bits 48..63 of DecodeState::tick) and the CTA's change of
+// the nonzero count plus 2^31 to bits 0..47 (at most 2^16 CTAs, so the biased
+// sum stays below 2^47), so that the last CTA learns |supp x'| = nnz0 + the
+// changes from the atomic's own return value and reads more state only when
+// H_k has to run.  That CTA stores the round's change in nnz_delta (read by the
+// accept step) and clears the ticket.  nnz0: |supp x_hat| at the round's start.
+#define RL0_TICK_BIAS (1ull << 31)
+
+__device__ __forceinline__ unsigned long long cta_ticket64(unsigned long long *ctr, unsigned long long add)
+{
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(ctr), "l"(add) : "memory");
+    return old;
+}
+
+template <int NT>
+__device__ __forceinline__ void last_cta_hk_tick(const KArgs &a, const DecodeCtx *ctx, HkShared &hk, unsigned *suf,
+                                                 int *go, int cta_dn, unsigned nnz0)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long mine = (1ull << 48) + (unsigned long long)((long long)cta_dn + (long long)RL0_TICK_BIAS);
+        const unsigned long long v = cta_ticket64(&a.st->tick, mine) + mine;
+        int run = 0;
+        if ((unsigned)(v >> 48) == gridDim.x) {
+            DecodeState *stw = a.st;
+            const long long dn = (long long)(v & ((1ull << 48) - 1ull)) - (long long)gridDim.x * (long long)RL0_TICK_BIAS;
+            stw->tick = 0ull;
+            stw->nnz_delta = (int)dn;
+            run = ((long long)nnz0 + dn > ctx->k) && __ldcg(&stw->upd_count) != 0u && __ldcg(&stw->status) == 0;
+        }
+        *go = run;
+    }
+    __syncthreads();
+    if (!*go) return;
+    cta_hk_select<NT>(a.list, __ldcg(&a.st->list_count), ctx->x, ctx->k, a.hkkey, a.dlog, &a.st->drop_count, hk, suf);
+}
+
 // ---------------------------------------------------------------------------
 // The rebuild's row buckets.  Row i's contributors to r = y - A x' are kept in
 // two kinds of buckets of RL0_BUCKET column ids:

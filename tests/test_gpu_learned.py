@@ -239,10 +239,28 @@ def test_learned_round_step_matches_oracle(rl0, trained):
     assert near_total <= 2 + dec_total // 1000
 
 
+def _analytic_restart(rl0, A, y, k, sn, x0, rounds=40):
+    """A second analytic sweep of Algorithm 2 from x0 (round steps, the accept test on
+    ||r||_1, the noise stop level): the control for the learned decode's analytic
+    continuation."""
+    xh = x0.clone()
+    rh = y - rl0.sketch(A, xh, sigma_n=0.0)
+    l1h = float(rh.abs().double().sum())
+    for r in range(1, rounds):
+        xp, rp, _, l1 = rl0.round_step(A, y, k, r, xh, rh, want_passed=False, sigma_n=sn)
+        if l1 < l1h:
+            xh, rh, l1h = xp, rp, l1
+        if l1h <= A.m * sn * math.sqrt(2 / math.pi):
+            break
+    return xh
+
+
 def test_trained_scorer_against_the_analytic_rule(rl0, trained):
     """Held-out instances: recovery (success condition of Section 'Stopping conditions'),
-    rounds and decode time, learned vs analytic; and the learned decode against the oracle's
-    learned decode."""
+    rounds and decode time, learned vs analytic and vs the analytic rule given a second
+    sweep from its own result (so that the learned decode's analytic continuation is not
+    what makes the difference); and the learned decode against the oracle's learned
+    decode."""
     rng = np.random.default_rng(12)
     n, d = 1 << 14, 7
     wb, bits = trained["wb"], trained["bits"]
@@ -254,8 +272,10 @@ def test_trained_scorer_against_the_analytic_rule(rl0, trained):
         y = torch.from_numpy(y32).cuda()
         xa, sa = rl0.decode(A, y, k, sigma_n=sn)
         xl, sl = rl0.decode(A, y, k, sigma_n=sn, scorer=1, mlp=wb)
+        xr = _analytic_restart(rl0, A, y, k, sn, xa)
         res.append((_success(xa.cpu().numpy(), I.x, m, sn), _success(xl.cpu().numpy(), I.x, m, sn),
-                    sa["rounds"], sl["rounds"], sa["ms"], sl["ms"], sl["analytic_rounds"]))
+                    sa["rounds"], sl["rounds"], sa["ms"], sl["ms"], sl["analytic_rounds"],
+                    _success(xr.cpu().numpy(), I.x, m, sn)))
         if i < 3:
             xo, so, lo = oracle.decode(I.rows, y32.astype(np.float64), k, sigma_n=sn, mlp_bf16=bits)
             xg = xl.cpu().numpy().astype(np.float64)
@@ -264,13 +284,16 @@ def test_trained_scorer_against_the_analytic_rule(rl0, trained):
                         sl["analytic_rounds"], so["analytic_rounds"],
                         [e["updated"] for e in rl0.decode_log(A)], [e["updated"] for e in lo]))
     res = np.array(res, dtype=float)
-    print("\nanalytic: success %.2f rounds %.1f ms %.3f | learned: success %.2f rounds %.1f ms %.3f "
-          "(analytic continuation rounds %.1f)" % (res[:, 0].mean(), res[:, 2].mean(), res[:, 4].mean(),
-                                                    res[:, 1].mean(), res[:, 3].mean(), res[:, 5].mean(),
-                                                    res[:, 6].mean()))
+    print("\nanalytic: success %.2f (with a second sweep %.2f) rounds %.1f ms %.3f | learned: success %.2f "
+          "rounds %.1f ms %.3f (analytic continuation rounds %.1f)"
+          % (res[:, 0].mean(), res[:, 7].mean(), res[:, 2].mean(), res[:, 4].mean(), res[:, 1].mean(),
+             res[:, 3].mean(), res[:, 5].mean(), res[:, 6].mean()))
     for p_ in par:
         print("parity: support %s rel %.2e rounds %d/%d cont %d/%d\n  gpu %s\n  orc %s" % p_)
-    assert res[:, 1].mean() >= res[:, 0].mean()           # no loss of recovery
+    # the trained network recovers strictly more held-out instances than the analytic
+    # rule, with or without the analytic rule's second sweep, and loses none
+    assert res[:, 1].mean() > max(res[:, 0].mean(), res[:, 7].mean())
+    assert np.all(res[:, 1] >= res[:, 0])
     for p_ in par:
         assert p_[0] and p_[1] <= 1e-5
 
