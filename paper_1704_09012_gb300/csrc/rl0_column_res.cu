@@ -114,9 +114,11 @@ struct ResScratch {
     unsigned char it_ok[NT * DMAX];
     float it_w[NT * DMAX];
     float it_sc[NT * DMAX];              // n_e - n_z of the item
-    float feat[LEARNED ? NT : 1][RL0_NFEAT];   // learned scorer: features of NT items at a time
+    float feat[LEARNED ? NT : 1][RL0_NFEAT];   // learned scorer: features of the items that pass the
+    unsigned short fidx[LEARNED ? NT : 1];     // exact tests (compact, NT items at a time) and their items
     float q[NT][DMAX];                   // q_e of (item, slot l), NT items at a time
     unsigned wsum[NT / 32];
+    int nf;
 };
 
 // Exclusive prefix over the CTA of v (NT threads, all of them call it);
@@ -341,6 +343,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     __syncthreads();                               // the stream is done: the codes' bytes become scratch
     const int count = min(S.count, hi - lo);
     ResScratch<DMAX, NT, LEARNED> &R = *(ResScratch<DMAX, NT, LEARNED> *)dsm;
+    if (LEARNED && tid == 0) R.nf = 0;              // first read after the batch's barriers
     const float alpha = ctx->alpha;
     for (int b0 = 0; b0 < count; b0 += NT) {
         // one thread per listed column: FP32 residuals, exact candidates
@@ -423,17 +426,24 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
                 float lhs = 0.0f;
                 for (int l = 0; l < d; ++l) lhs += fabsf(R.r[l][ee] - w);
                 if constexpr (LEARNED) {
-                    // the learned scorer: the l1 test and n_e - n_z >= 1.5 here, the
-                    // network's logit below
-                    R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= ctx->learned_need) ? 1 : 0;
-                    AnchorEval E;
-                    E.ne = ne;
-                    E.w = w;
-                    E.lhs = lhs;
-                    float f[RL0_NFEAT];
-                    candidate_features(&R.r[0][ee], NT, d, E, R.nz[ee], R.rhs[ee], ctx->inv_sn, th.t, ctx->drho, f);
+                    // the learned scorer: the l1 test and n_e - n_z >= 1.5 here; the
+                    // features of the items that pass go to a compact list, whose
+                    // logits the network takes below
+                    const bool ok = lhs <= R.rhs[ee] && ne - R.nz[ee] >= ctx->learned_need;
+                    R.it_ok[k] = ok ? 1 : 0;
+                    if (ok) {
+                        AnchorEval E;
+                        E.ne = ne;
+                        E.w = w;
+                        E.lhs = lhs;
+                        float f[RL0_NFEAT];
+                        candidate_features(&R.r[0][ee], NT, d, E, R.nz[ee], R.rhs[ee], ctx->inv_sn, th.t, ctx->drho,
+                                           f);
+                        const int p = atomicAdd(&R.nf, 1);
 #pragma unroll
-                    for (int q = 0; q < RL0_NFEAT; ++q) R.feat[kk][q] = f[q];
+                        for (int q = 0; q < RL0_NFEAT; ++q) R.feat[p][q] = f[q];
+                        R.fidx[p] = (unsigned short)kk;
+                    }
                 } else {
                     R.it_ok[k] = (lhs <= R.rhs[ee] && ne - R.nz[ee] >= alpha) ? 1 : 0;
                 }
@@ -442,19 +452,21 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
             }
             __syncthreads();
             if constexpr (LEARNED) {
-                // the items' logits, 16 per warp on the tensor cores
+                // the passing items' logits, 16 per warp on the tensor cores
+                const unsigned nf = (unsigned)R.nf;
                 const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
-                for (unsigned t0 = (unsigned)(tid >> 5) * 16u; t0 < kn; t0 += (NT / 32) * 16u) {
-                    auto f = [&](int r, int i) { return (t0 + r < kn) ? R.feat[t0 + r][i] : 0.0f; };
+                for (unsigned t0 = (unsigned)(tid >> 5) * 16u; t0 < nf; t0 += (NT / 32) * 16u) {
+                    auto f = [&](int r, int i) { return (t0 + r < nf) ? R.feat[t0 + r][i] : 0.0f; };
                     float lo, hi;
                     warp_mlp_logits16(f, wb, &lo, &hi);
                     if ((tid & 3) == 0) {
                         const unsigned gr = (unsigned)((tid & 31) >> 2);
-                        if (t0 + gr < kn && !(lo >= ctx->logit_thr)) R.it_ok[k0 + t0 + gr] = 0;
-                        if (t0 + gr + 8 < kn && !(hi >= ctx->logit_thr)) R.it_ok[k0 + t0 + gr + 8] = 0;
+                        if (t0 + gr < nf && !(lo >= ctx->logit_thr)) R.it_ok[k0 + R.fidx[t0 + gr]] = 0;
+                        if (t0 + gr + 8 < nf && !(hi >= ctx->logit_thr)) R.it_ok[k0 + R.fidx[t0 + gr + 8]] = 0;
                     }
                 }
                 __syncthreads();
+                if (tid == 0) R.nf = 0;                // read again only after the next batch's barriers
             }
         }
         // each column: its first passing item is its highest passing slot (the

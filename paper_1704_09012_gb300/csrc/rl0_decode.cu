@@ -195,8 +195,8 @@ struct ColShared {
             unsigned short q[NT];              // this pass's queue: (column lane << 5) | slot
             float score[NT], w[NT];
             unsigned char ok[NT];
-            float f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the queued candidates
-            unsigned char l1ok[LEARNED ? NT : 1];
+            float f[LEARNED ? RL0_NFEAT : 1][LEARNED ? NT : 1];   // features of the candidates that pass
+            unsigned short fq[LEARNED ? NT : 1];                  // their queue positions
         } c;
         struct {
             HkShared hk;
@@ -204,7 +204,7 @@ struct ColShared {
         } h;
     };
     Series pe;
-    int nq;
+    int nq, nf;
     int last;
 };
 
@@ -214,6 +214,7 @@ __device__ __forceinline__ void col_setup(const DecodeCtx *ctx, ColShared<DMAX, 
     const int tid = threadIdx.x;
     if (tid == 0) {
         S.nq = 0;
+        S.nf = 0;
         if (!IND) S.pe = ctx->pe;
     }
     // (these shared copies are first read after a barrier of the tile body)
@@ -264,38 +265,46 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
         __syncthreads();
         const int nq = S.nq;
         if (LEARNED) {
-            // the learned scorer's logit replaces n_e - n_z >= alpha: features of
-            // every queued candidate, then the MLP over 32-candidate slices with
-            // one thread per (candidate, hidden unit); the FMA chains are those
-            // of mlp_logit, so the logits equal rl0_mlp_forward's
+            // the learned scorer's logit replaces n_e - n_z >= alpha: each queued
+            // candidate's exact l1 test and n_e - n_z >= 1.5 first; the features
+            // of those that pass go to a compact list, whose logits the MLP takes
+            // 16 per warp on the tensor cores (rl0_mma.cuh: the arithmetic of
+            // rl0_mlp_forward); a candidate passes when its logit reaches the
+            // threshold
             for (int e = tid; e < nq; e += NT) {
                 const int owner = S.c.q[e] >> 5, s = S.c.q[e] & 31;
                 const AnchorEval E = eval_anchor<IND>(&S.c.r[0][owner], NT, d, s, th.te, S.pe);
-                float f[RL0_NFEAT];
-                candidate_features(&S.c.r[0][owner], NT, d, E, S.c.nz[owner], S.c.rhs[owner], ctx->inv_sn, th.t,
-                                   ctx->drho, f);
-#pragma unroll
-                for (int q = 0; q < RL0_NFEAT; ++q) S.c.f[q][e] = f[q];
-                S.c.l1ok[e] = (E.lhs <= S.c.rhs[owner] && E.ne - S.c.nz[owner] >= ctx->learned_need) ? 1 : 0;
+                S.c.ok[e] = 0;
+                S.c.score[e] = 0.0f;
                 S.c.w[e] = E.w;
+                if (E.lhs <= S.c.rhs[owner] && E.ne - S.c.nz[owner] >= ctx->learned_need) {
+                    const int p = atomicAdd(&S.nf, 1);
+                    float f[RL0_NFEAT];
+                    candidate_features(&S.c.r[0][owner], NT, d, E, S.c.nz[owner], S.c.rhs[owner], ctx->inv_sn,
+                                       th.t, ctx->drho, f);
+#pragma unroll
+                    for (int q = 0; q < RL0_NFEAT; ++q) S.c.f[q][p] = f[q];
+                    S.c.fq[p] = (unsigned short)e;
+                }
             }
             __syncthreads();
-            // the queued candidates' logits, 16 per warp on the tensor cores
-            // (rl0_mma.cuh: the arithmetic of rl0_mlp_forward)
+            const int nf = S.nf;
             const __nv_bfloat16 *wb = (const __nv_bfloat16 *)ctx->mlp;
-            for (int e0 = (tid >> 5) * 16; e0 < nq; e0 += (NT / 32) * 16) {
-                auto f = [&](int r, int i) { return (e0 + r < nq) ? S.c.f[i][e0 + r] : 0.0f; };
+            for (int e0 = (tid >> 5) * 16; e0 < nf; e0 += (NT / 32) * 16) {
+                auto f = [&](int r, int i) { return (e0 + r < nf) ? S.c.f[i][e0 + r] : 0.0f; };
                 float lo, hi;
                 warp_mlp_logits16(f, wb, &lo, &hi);
                 if ((tid & 3) == 0) {
                     const int gr = (tid & 31) >> 2;
-                    if (e0 + gr < nq) {
-                        S.c.score[e0 + gr] = lo;
-                        S.c.ok[e0 + gr] = (S.c.l1ok[e0 + gr] && lo >= ctx->logit_thr) ? 1 : 0;
+                    if (e0 + gr < nf) {
+                        const int e = S.c.fq[e0 + gr];
+                        S.c.score[e] = lo;
+                        S.c.ok[e] = (lo >= ctx->logit_thr) ? 1 : 0;
                     }
-                    if (e0 + gr + 8 < nq) {
-                        S.c.score[e0 + gr + 8] = hi;
-                        S.c.ok[e0 + gr + 8] = (S.c.l1ok[e0 + gr + 8] && hi >= ctx->logit_thr) ? 1 : 0;
+                    if (e0 + gr + 8 < nf) {
+                        const int e = S.c.fq[e0 + gr + 8];
+                        S.c.score[e] = hi;
+                        S.c.ok[e] = (hi >= ctx->logit_thr) ? 1 : 0;
                     }
                 }
             }
@@ -321,7 +330,10 @@ __device__ __forceinline__ void score_tile(const KArgs &a, const DecodeCtx *ctx,
                 bsc = S.c.score[my];
             }
         }
-        if (tid == 0) S.nq = 0;
+        if (tid == 0) {
+            S.nq = 0;
+            S.nf = 0;
+        }
     }
     commit_column(a, ctx, j, active, best, bw);
 }

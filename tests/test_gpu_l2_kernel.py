@@ -1,0 +1,121 @@
+"""The L2-gather column kernel against the FP64 oracle.
+
+An instance whose residual codes do not fit in a CTA's shared memory (2 bytes per row:
+m = 209 715 rows take 419 KB, the limit is 227 KB) runs its column score on the kernel
+that gathers (r, p_z) from L2 instead of the resident-code kernel: n = 2^21, delta = 0.1,
+rho = 0.15, d = 7, SNR 30 dB, the shape of the learned scorer's evaluation workload at
+half its size.  Round steps from perturbed states with the analytic rule (Algorithm 2)
+and with a trained scorer, and one whole learned decode, each against the oracle."""
+import numpy as np
+import pytest
+
+import gm
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 1 << 21
+
+
+@pytest.fixture(scope="module")
+def rl0():
+    import paper_1704_09012_gb300 as m
+    m._lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def inst():
+    m = int(0.1 * N)
+    k = int(0.15 * m)
+    sn = gm.sigma_from_snr(7, k / m, 30.0)
+    I = gm.instance(N, m, k, 7, sn, 2121)
+    y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
+    return I, y.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def scorer(rl0):
+    """A scorer trained on the decode logs of two analytic decodes at n = 2^14 (same
+    delta, rho, SNR)."""
+    from paper_1704_09012_gb300 import learned
+    F, Y = [], []
+    for i in range(2):
+        n = 1 << 14
+        m = int(0.1 * n)
+        k = int(0.15 * m)
+        sn = gm.sigma_from_snr(7, k / m, 30.0)
+        I = gm.instance(n, m, k, 7, sn, 3100 + i)
+        y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
+        A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), m)
+        f, lab = learned.decode_log_samples(A, torch.from_numpy(y.astype(np.float32)).cuda(), k,
+                                            torch.from_numpy(I.x).cuda(), sn)
+        F.append(f)
+        Y.append(lab)
+    wb, _, _ = learned.train_scorer(torch.cat(F), torch.cat(Y), epochs=6)
+    return wb, wb.cpu().numpy().view(np.uint16)
+
+
+def _state(I, y32, frac_shift, frac_drop, seed):
+    rng = np.random.default_rng(seed)
+    x = I.x.astype(np.float64).copy()
+    sh = rng.choice(I.support, int(frac_shift * I.k), replace=False)
+    x[sh] += rng.choice([-1, 1], sh.size) * rng.uniform(0.2, 1.0, sh.size)
+    x[rng.choice(I.support, int(frac_drop * I.k), replace=False)] = 0.0
+    x32 = x.astype(np.float32)
+    r32 = (y32.astype(np.float64) - oracle.sketch(I.rows, x32.astype(np.float64), I.m)).astype(np.float32)
+    return x32, r32
+
+
+@pytest.mark.parametrize("learned_rule", [False, True])
+def test_round_step_on_the_l2_kernel_matches_oracle(rl0, inst, scorer, learned_rule):
+    I, y32 = inst
+    assert 2 * I.m > 227 * 1024                      # the codes cannot be resident
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
+    wb, bits = scorer
+    g_extra = dict(scorer=1, mlp=wb) if learned_rule else {}
+    o_extra = dict(mlp_bf16=bits) if learned_rule else {}
+    margin = 1e-3 if learned_rule else 1e-4
+    passes = near_total = dec_total = 0
+    with oracle.openmp():
+        for trial, ridx in enumerate((3, 12, 24)):
+            x32, r32 = _state(I, y32, 0.25, 0.3 + 0.1 * trial, 40 + trial)
+            xo, ro, upd, rec = oracle.round_step(I.rows, y32.astype(np.float64), I.k, ridx, x32.astype(np.float64),
+                                                 r32.astype(np.float64), sigma_n=I.sigma_n, **o_extra)
+            xg, rg, passed, l1g = rl0.round_step(A, torch.from_numpy(y32).cuda(), I.k, ridx,
+                                                 torch.from_numpy(x32).cuda(), torch.from_numpy(r32).cuda(),
+                                                 sigma_n=I.sigma_n, **g_extra)
+            pg = passed.cpu().numpy().astype(bool)
+            po = rec["passed"].astype(bool)
+            near = rec["min_margin"] < margin
+            assert np.array_equal(pg[~near], po[~near])
+            near_total += int(near.sum())
+            dec_total += near.size
+            passes += int(po.sum())
+            if np.array_equal(pg, po):
+                xg = xg.cpu().numpy().astype(np.float64)
+                assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+                assert np.linalg.norm(xg - xo) <= 1e-5 * np.linalg.norm(xo)
+                assert l1g == pytest.approx(np.abs(ro).sum(), rel=1e-6)
+    # decisions within the margin of the threshold: at most one in a thousand
+    assert passes > 1000
+    assert near_total <= 3 + dec_total // 1000
+
+
+def test_learned_decode_on_the_l2_kernel_matches_oracle(rl0, inst, scorer):
+    I, y32 = inst
+    A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
+    wb, bits = scorer
+    xl, sl = rl0.decode(A, torch.from_numpy(y32).cuda(), I.k, sigma_n=I.sigma_n, scorer=1, mlp=wb)
+    with oracle.openmp():
+        xo, so, _ = oracle.decode(I.rows, y32.astype(np.float64), I.k, sigma_n=I.sigma_n, mlp_bf16=bits)
+    xg = xl.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print("\nlearned n=2^21 on the L2 kernel: rounds %d/%d (continuation %d/%d) accepted %d/%d rel_l2 %.2e" % (
+        sl["rounds"], so["rounds"], sl["analytic_rounds"], so["analytic_rounds"], sl["accepted_rounds"],
+        so["accepted_rounds"], rel))
+    assert np.array_equal(np.nonzero(xg)[0], np.nonzero(xo)[0])
+    assert rel <= 1e-5
+    assert sl["rounds"] == so["rounds"] and sl["analytic_rounds"] == so["analytic_rounds"]
+    assert sl["accepted_rounds"] == so["accepted_rounds"]
