@@ -228,6 +228,33 @@ def l2_copy_peak(torch, sizes_mib=(8, 16, 32), back_to_back=20, reps=10):
     return best
 
 
+def l2_read_peak(torch, sizes_mib=(16, 32, 64), back_to_back=20, reps=10):
+    """L2-resident read bandwidth (GB/s): `back_to_back` reductions a.sum() of one buffer
+    of each size in `sizes_mib` MiB (inside the 129 MB L2) between one pair of CUDA
+    events, best over sizes and `reps` repetitions.  The reduction writes one scalar, so
+    the bytes are reads.  Returns (GB/s, buffer MiB of the best)."""
+    best = (0.0, None)
+    stream = torch.cuda.current_stream()
+    for mib in sizes_mib:
+        n = (mib << 20) // 4
+        a = torch.ones(n, dtype=torch.float32, device="cuda")
+        out = torch.empty((), dtype=torch.float32, device="cuda")
+        for _ in range(5):
+            torch.sum(a, out=out)
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(back_to_back):
+                torch.sum(a, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gbs = back_to_back * n * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+            if gbs > best[0]:
+                best = (gbs, mib)
+        del a
+    return best
+
+
 def bench_batched(rl0, torch, count, steps, flush, plain=True):
     """The batched workload: `count` independent instances, n uniform over [2^10, 2^16],
     delta in [0.1, 0.3], rho in [0.05, 0.2], d = 7, SNR in [30, 60] dB, continuous scores,
@@ -688,6 +715,7 @@ def main():
         peak = 6800.0
     group_ms = {g: sum(p["ms_" + g] for p in prof) / len(prof) for g in ("score", "hk", "rebuild", "accept")}
     l2_peak = l2_copy_peak(torch)
+    l2_read = l2_read_peak(torch)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -704,9 +732,14 @@ def main():
                      "traffic": traffic_for("k_column_score_res"), "alg_bytes_per_launch": alg_bytes,
                      "avg_launch_ms": ms_score,
                      # inside a decode the row ids stay in L2 after the first round: the same
-                     # bytes against the L2-resident copy bandwidth measured here
-                     "l2": {"peak": l2_peak[0], "unit": "GB/s", "frac": achieved / l2_peak[0],
-                            "peak_source": "measured: L2-resident copies, 20 back to back, 2 x %d MiB" % l2_peak[1]}},
+                     # bytes (reads) against the L2-resident read bandwidth measured here, and
+                     # the copy (read + write) bandwidth beside it
+                     "l2": {"peak": l2_read[0], "unit": "GB/s", "frac": achieved / l2_read[0],
+                            "peak_source": "measured: L2-resident reads, 20 reductions back to back of %d MiB"
+                                           % l2_read[1],
+                            "copy_peak": l2_peak[0],
+                            "copy_peak_source": "measured: L2-resident copies, 20 back to back, 2 x %d MiB"
+                                                % l2_peak[1]}},
         "kernel_group_ms_per_decode": group_ms,
         "clocks": clk.summary(),
         "wall_s": t_wall,

@@ -173,12 +173,29 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     int j0 = lo;
     // row ids of this thread's first column(s): j0 + tid (and j0 + NT + tid
     // when paired), loaded while the previous kernel finishes (A never changes)
+    // paired with even n: the two columns of a thread are adjacent (j, j + 1
+    // from the even column below lo), so that each slot's two row ids come in
+    // one 8-byte load; otherwise they are j and j + NT
+    const bool vec = PAIRED && (n & 1) == 0;
     int nxt[DMAX], nxb[PAIRED ? DMAX : 1];
 #pragma unroll
     for (int s = 0; s < DMAX; ++s) {
-        const int j = j0 + tid;
-        nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
-        if constexpr (PAIRED) nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
+        if constexpr (PAIRED) {
+            if (vec) {
+                const int j = (lo & ~1) + 2 * tid;
+                const int2 v = (j < hi) ? __ldg(reinterpret_cast<const int2 *>(a.rows_sm + (size_t)s * n + j))
+                                        : make_int2(0, 0);
+                nxt[s] = v.x;
+                nxb[s] = v.y;
+            } else {
+                const int j = j0 + tid;
+                nxt[s] = (j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+                nxb[s] = (j + NT < hi) ? __ldg(a.rows_sm + (size_t)s * n + j + NT) : 0;
+            }
+        } else {
+            const int j = j0 + tid;
+            nxt[s] = (s < d && j < hi) ? __ldg(a.rows_sm + (size_t)s * n + j) : 0;
+        }
     }
     pdl_wait();                                    // the previous rebuild's r, codes, x and state
     // done, cur and round in one L2 trip (the code copy waits on cur)
@@ -268,26 +285,10 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         }
     };
     if constexpr (PAIRED) {
-        // two columns per thread, j and j + NT, bounded side by side in FP16
-        // lanes; a listed column reads its row ids again (from L2)
+        // two columns per thread bounded side by side in FP16 lanes; a listed
+        // column reads its row ids again (from L2)
         const CodeThr2 ct2 = code_thresholds2(ct, need);
-        for (; j0 < hi; j0 += 2 * NT) {
-            int ra[DMAX], rb[DMAX];
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s) {
-                ra[s] = nxt[s];
-                rb[s] = nxb[s];
-            }
-            {
-                const int jn = j0 + 2 * NT + tid;
-#pragma unroll
-                for (int s = 0; s < DMAX; ++s) {
-                    if (jn < hi) nxt[s] = __ldg(a.rows_sm + (size_t)s * n + jn);
-                    if (jn + NT < hi) nxb[s] = __ldg(a.rows_sm + (size_t)s * n + jn + NT);
-                }
-            }
-            const int ja = j0 + tid, jb = ja + NT;
-            const bool aa = ja < hi, ab = jb < hi;
+        auto pair_body = [&](const int *ra, const int *rb, int ja, int jb, bool aa, bool ab) {
             unsigned ma, mb;
             code_candidates2<DMAX, IND>(s_code, s_pz, ra, rb, aa, ab, ct2, ma, mb);
             const unsigned ba = __ballot_sync(0xffffffffu, ma != 0u), bb = __ballot_sync(0xffffffffu, mb != 0u);
@@ -313,6 +314,50 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
                 if (aa && !ma) passed[ja] = 0;
                 if (ab && !mb) passed[jb] = 0;
             }
+        };
+        if (vec) {
+            // columns jp + 2 tid and jp + 2 tid + 1; the one below lo (when lo is
+            // odd) belongs to the previous CTA and is masked
+            for (int jp = (j0 < hi) ? (lo & ~1) : hi; jp < hi; jp += 2 * NT) {
+                int ra[DMAX], rb[DMAX];
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s) {
+                    ra[s] = nxt[s];
+                    rb[s] = nxb[s];
+                }
+                {
+                    const int jn = jp + 2 * NT + 2 * tid;
+#pragma unroll
+                    for (int s = 0; s < DMAX; ++s) {
+                        if (jn < hi) {
+                            const int2 v = __ldg(reinterpret_cast<const int2 *>(a.rows_sm + (size_t)s * n + jn));
+                            nxt[s] = v.x;
+                            nxb[s] = v.y;
+                        }
+                    }
+                }
+                const int ja = jp + 2 * tid;
+                pair_body(ra, rb, ja, ja + 1, ja >= lo && ja < hi, ja + 1 < hi);
+            }
+            j0 = hi;
+        }
+        for (; j0 < hi; j0 += 2 * NT) {
+            int ra[DMAX], rb[DMAX];
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s) {
+                ra[s] = nxt[s];
+                rb[s] = nxb[s];
+            }
+            {
+                const int jn = j0 + 2 * NT + tid;
+#pragma unroll
+                for (int s = 0; s < DMAX; ++s) {
+                    if (jn < hi) nxt[s] = __ldg(a.rows_sm + (size_t)s * n + jn);
+                    if (jn + NT < hi) nxb[s] = __ldg(a.rows_sm + (size_t)s * n + jn + NT);
+                }
+            }
+            const int ja = j0 + tid, jb = ja + NT;
+            pair_body(ra, rb, ja, jb, ja < hi, jb < hi);
         }
     }
     for (; j0 < hi; j0 += NT) {
