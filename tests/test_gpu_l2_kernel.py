@@ -3,9 +3,10 @@
 An instance whose residual codes do not fit in a CTA's shared memory (2 bytes per row:
 m = 209 715 rows take 419 KB, the limit is 227 KB) runs its column score on the kernel
 that gathers (r, p_z) from L2 instead of the resident-code kernel: n = 2^21, delta = 0.1,
-rho = 0.15, d = 7, SNR 30 dB, the shape of the learned scorer's evaluation workload at
-half its size.  Round steps from perturbed states with the analytic rule (Algorithm 2)
-and with a trained scorer, and one whole learned decode, each against the oracle."""
+rho = 0.15, SNR 30 dB, d = 7 (the shape of the learned scorer's evaluation workload at
+half its size) and d = 12.  Round steps from perturbed states with the analytic rule
+(Algorithm 2) and with a trained scorer, and one whole learned decode, each against the
+oracle."""
 import numpy as np
 import pytest
 
@@ -25,14 +26,18 @@ def rl0():
     return m
 
 
-@pytest.fixture(scope="module")
-def inst():
-    m = int(0.1 * N)
-    k = int(0.15 * m)
-    sn = gm.sigma_from_snr(7, k / m, 30.0)
-    I = gm.instance(N, m, k, 7, sn, 2121)
-    y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
-    return I, y.astype(np.float32)
+_INST = {}
+
+
+def _inst(d):
+    if d not in _INST:
+        m = int(0.1 * N)
+        k = int(0.15 * m)
+        sn = gm.sigma_from_snr(d, k / m, 30.0)
+        I = gm.instance(N, m, k, d, sn, 2121 + d)
+        y = oracle.sketch(I.rows, I.x.astype(np.float64), m) + I.eta.astype(np.float64)
+        _INST[d] = (I, y.astype(np.float32))
+    return _INST[d]
 
 
 @pytest.fixture(scope="module")
@@ -68,9 +73,9 @@ def _state(I, y32, frac_shift, frac_drop, seed):
     return x32, r32
 
 
-@pytest.mark.parametrize("learned_rule", [False, True])
-def test_round_step_on_the_l2_kernel_matches_oracle(rl0, inst, scorer, learned_rule):
-    I, y32 = inst
+@pytest.mark.parametrize("d,learned_rule", [(7, False), (7, True), (12, False)])
+def test_round_step_on_the_l2_kernel_matches_oracle(rl0, scorer, d, learned_rule):
+    I, y32 = _inst(d)
     assert 2 * I.m > 227 * 1024                      # the codes cannot be resident
     A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
     wb, bits = scorer
@@ -103,8 +108,8 @@ def test_round_step_on_the_l2_kernel_matches_oracle(rl0, inst, scorer, learned_r
     assert near_total <= 3 + dec_total // 1000
 
 
-def test_learned_decode_on_the_l2_kernel_matches_oracle(rl0, inst, scorer):
-    I, y32 = inst
+def test_learned_decode_on_the_l2_kernel_matches_oracle(rl0, scorer):
+    I, y32 = _inst(7)
     A = rl0.Expander.from_rows(torch.from_numpy(I.rows).cuda(), I.m)
     wb, bits = scorer
     xl, sl = rl0.decode(A, torch.from_numpy(y32).cuda(), I.k, sigma_n=I.sigma_n, scorer=1, mlp=wb)
