@@ -253,6 +253,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
     // the count the code bound must allow: Alg. 2's alpha, or the learned
     // scorer's candidate threshold (the slack covers FP32 rounding of n_e)
     const float need0 = LEARNED ? ctx->learned_need : ctx->alpha;
+    const int rule = ctx->anchor_rule;            // read by the resolve; loaded here, off its path
     const float need = IND ? need0 : need0 - 1e-3f;
     int32_t *passed = ctx->passed;
     const int lane = tid & 31;
@@ -519,7 +520,6 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         // of largest n_e - n_z, ties to the lower slot (items come highest first)
         int best = -1;
         float bw = 0.0f, bsc = 0.0f;
-        const int rule = ctx->anchor_rule;
         for (unsigned q = 0; q < nc; ++q)
             if (R.it_ok[off + q]) {
                 if (rule == 0) {

@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
     pdl_launch_dependents();
     if (done) return;
     const int no_accept = ctx->no_accept;
+    const float conv_tol = ctx->conv_tol;
     if (upd == 0) {                                // nothing changed: r = r_hat, only t advances
         if (blockIdx.x == 0 && !no_accept) accept_step<RL0_ROWS_CHUNK>(a, 0u, s_scan);
         return;
@@ -408,8 +409,8 @@ __global__ void __launch_bounds__(RL0_ROWS_CHUNK) k_rebuild(KArgs a)
         a.l1part[blockIdx.x] = s2.x;
         a.final_part[(size_t)(cur ? 0 : 1) * a.nchunks + blockIdx.x] = s2.y;
     }
-    if (ctx->conv_tol > 0.0f) {                    // Alg. 1: rows of r' not yet zero
-        const int big = __syncthreads_count(i < a.m && !(l1.hi <= ctx->conv_tol));
+    if (conv_tol > 0.0f) {                         // Alg. 1: rows of r' not yet zero
+        const int big = __syncthreads_count(i < a.m && !(l1.hi <= conv_tol));
         if (threadIdx.x == 0 && big) atomicAdd(&st->big_cand, (unsigned)big);
     }
     if (no_accept) return;

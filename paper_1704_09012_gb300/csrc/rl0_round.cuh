@@ -206,6 +206,7 @@ __device__ __forceinline__ void last_cta_hk_tick(const KArgs &a, const DecodeCtx
 {
     __syncthreads();
     if (threadIdx.x == 0) {
+        const long long k = ctx->k;                 // loaded before the ticket's round trip
         const unsigned long long mine = (1ull << 48) + (unsigned long long)((long long)cta_dn + (long long)RL0_TICK_BIAS);
         const unsigned long long v = cta_ticket64(&a.st->tick, mine) + mine;
         int run = 0;
@@ -214,7 +215,7 @@ __device__ __forceinline__ void last_cta_hk_tick(const KArgs &a, const DecodeCtx
             const long long dn = (long long)(v & ((1ull << 48) - 1ull)) - (long long)gridDim.x * (long long)RL0_TICK_BIAS;
             stw->tick = 0ull;
             stw->nnz_delta = (int)dn;
-            run = ((long long)nnz0 + dn > ctx->k) && __ldcg(&stw->upd_count) != 0u && __ldcg(&stw->status) == 0;
+            run = ((long long)nnz0 + dn > k) && __ldcg(&stw->upd_count) != 0u && __ldcg(&stw->status) == 0;
         }
         *go = run;
     }
@@ -401,13 +402,24 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
     const DecodeCtx *ctx = a.ctx;
     float *x = ctx->x;
     if (t < SW) ((unsigned *)&S)[t] = __ldcg((const unsigned *)st + t);
+    // the per-call settings thread 0 decides with, loaded beside the state
+    // words (read later, after stores to global memory, each would be a
+    // dependent L2 trip of its own)
+    int c_always = 0, c_log = 0, c_nrounds = 0;
+    double c_stop = 0.0;
+    if (t == 0) {
+        c_always = ctx->always_accept;
+        c_log = ctx->want_log;
+        c_nrounds = ctx->nrounds;
+        c_stop = ctx->stop_level;
+    }
     // ||r||_1 of the candidate: chunk partials combined in a fixed order
     const double v = (upd > 0) ? cta_sum_parts_l2<NT>(a.l1part, a.nchunks, s_parts) : 0.0;
     __syncthreads();
     if (t == 0) {
         S.rb_done = 0u;                            // the rebuild's last-CTA count starts over
         s_l1 = v;
-        s_acc = (upd > 0) ? (ctx->always_accept ? 1 : (v < S.l1_hat)) : 0;
+        s_acc = (upd > 0) ? (c_always ? 1 : (v < S.l1_hat)) : 0;
     }
     __syncthreads();
     const int cur0 = S.cur;                        // r_hat's buffer during this round
@@ -478,7 +490,7 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
     if (t == 0) {
         const int round = S.round;
         const double l1n = (upd > 0) ? s_l1 : S.l1_hat;
-        if (ctx->want_log && round < RL0_MAX_ROUNDS) {
+        if (c_log && round < RL0_MAX_ROUNDS) {
             RoundLog L;
             L.l1_candidate = l1n;
             L.l1_hat = S.l1_hat;
@@ -501,16 +513,16 @@ __device__ void accept_step(const KArgs &a, unsigned upd, unsigned *shu)
         S.rounds_run += 1;
         S.iters += 1;
         S.l1_new = l1n;
-        if (ctx->always_accept) {
+        if (c_always) {
             // Alg. 1: every iteration is kept; it ends when one changes nothing
             if (upd > 0) S.big_hat = S.big_cand;
             S.converged = (S.big_hat == 0);
             if (upd == 0) S.done = 1;
         } else {
-            S.converged = (S.l1_hat <= ctx->stop_level);
+            S.converged = (S.l1_hat <= c_stop);
         }
         S.big_cand = 0;
-        if (S.converged || S.round >= ctx->nrounds || S.iters > (unsigned)ctx->nrounds || S.status != 0)
+        if (S.converged || S.round >= c_nrounds || S.iters > (unsigned)c_nrounds || S.status != 0)
             S.done = 1;
     }
     __syncthreads();
