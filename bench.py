@@ -240,12 +240,12 @@ def l2_read_peak(torch, sizes_mib=(16, 32, 64), back_to_back=20, reps=10):
         a = torch.ones(n, dtype=torch.float32, device="cuda")
         out = torch.empty((), dtype=torch.float32, device="cuda")
         for _ in range(5):
-            torch.sum(a, out=out)
+            torch.sum(a, dim=0, out=out)
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(back_to_back):
-                torch.sum(a, out=out)
+                torch.sum(a, dim=0, out=out)
             e1.record(stream)
             torch.cuda.synchronize()
             gbs = back_to_back * n * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
