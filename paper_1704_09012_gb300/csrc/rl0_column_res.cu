@@ -540,8 +540,22 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
             ctx->x[j] = nv;
         }
         if (passed && act) passed[j] = pass ? 1 : 0;
-        // the batch's commit: one global atomic per counter
+        // a column that became nonzero takes its rows' fresh-bucket slots now,
+        // so that those atomics travel with the commit's below
         const bool fresh = pass && old == 0.0f && nv != 0.0f;
+        int rid[DMAX], slot[DMAX];
+        if (fresh) {
+            if (e < qcap) {
+#pragma unroll
+                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? sq[e].rid[s2] : 0;
+            } else {
+                const int *ent = seg + (size_t)e * (DMAX + 2);
+#pragma unroll
+                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? __ldcg(ent + 2 + s2) : 0;
+            }
+            bucket_slots<DMAX>(a, rid, d, slot);
+        }
+        // the batch's commit: one global atomic per counter
         const unsigned pf = cta_exclusive_scan<NT>((pass ? 0x10000u : 0u) | (fresh ? 1u : 0u), R.wsum, &S.total);
         const unsigned tpf = S.total;
         // entries that became zero; the fresh ones are the scan's low field
@@ -563,16 +577,7 @@ __device__ __forceinline__ bool column_phase(const KArgs &a, unsigned char *dsm)
         }
         if (fresh) {
             a.list[S.fbase + (pf & 0xffffu)] = j;
-            int rid[DMAX];
-            if (e < qcap) {
-#pragma unroll
-                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? sq[e].rid[s2] : 0;
-            } else {
-                const int *ent = seg + (size_t)e * (DMAX + 2);
-#pragma unroll
-                for (int s2 = 0; s2 < DMAX; ++s2) rid[s2] = (s2 < d) ? __ldcg(ent + 2 + s2) : 0;
-            }
-            bucket_column<DMAX>(a, j, rid, d);
+            bucket_store<DMAX>(a, j, rid, d, slot);
         }
         __syncthreads();                           // the scratch is reused by the next batch
     }

@@ -83,20 +83,32 @@ __device__ __forceinline__ unsigned long long take_upd_list(DecodeState *st, uns
 
 // Column j, which became nonzero this round, into the fresh bucket of each of
 // its d rows (RL0_BUCKET per row; a fuller row sets the overflow flag, and
-// the rebuild then takes every row from CSR(A^T)).
-// The d <= DM atomics are issued before any store, so they overlap.
+// the rebuild then takes every row from CSR(A^T)), in two halves: the slots
+// (d <= DM atomics, issued before any store, so they overlap) and the stores.
 template <int DM>
-__device__ __forceinline__ void bucket_column(const KArgs &a, int j, const int *rid, int d)
+__device__ __forceinline__ void bucket_slots(const KArgs &a, const int *rid, int d, int *slot)
 {
-    int slot[DM];
 #pragma unroll
     for (int s = 0; s < DM; ++s) slot[s] = (s < d) ? atomicAdd(&a.bcnt[rid[s]], 1) : 0;
+}
+
+template <int DM>
+__device__ __forceinline__ void bucket_store(const KArgs &a, int j, const int *rid, int d, const int *slot)
+{
 #pragma unroll
     for (int s = 0; s < DM; ++s)
         if (s < d) {
             if (slot[s] < RL0_BUCKET) a.bkt[(long long)rid[s] * RL0_BUCKET + slot[s]] = j;
             else a.st->overflow = 1;
         }
+}
+
+template <int DM>
+__device__ __forceinline__ void bucket_column(const KArgs &a, int j, const int *rid, int d)
+{
+    int slot[DM];
+    bucket_slots<DM>(a, rid, d, slot);
+    bucket_store<DM>(a, j, rid, d, slot);
 }
 
 // Column j's outcome: x_j += omega of its chosen anchor (best >= 0), with the
