@@ -135,6 +135,15 @@ __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *c
         const unsigned gone = __popc(__ballot_sync(0xffffffffu, pass && old != 0.0f && nv == 0.0f));
         const bool fresh = pass && old == 0.0f && nv != 0.0f;
         const unsigned fmask = __ballot_sync(0xffffffffu, fresh);
+        // d <= 8: a fresh column's row ids and bucket slots, before (and so in
+        // flight with) the leader's atomic below
+        int rid[8], slot[8];
+        const bool early = fresh && a.d <= 8;
+        if (early) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) rid[q] = (q < a.d) ? __ldg(a.rows_sm + (size_t)q * a.n + j) : 0;
+            bucket_slots<8>(a, rid, a.d, slot);
+        }
         unsigned base = 0, fbase = 0;
         if (lane == leader) {
             if (dn) atomicAdd(&a.st->nnz_delta, dn);
@@ -152,7 +161,10 @@ __device__ __forceinline__ void commit_column(const KArgs &a, const DecodeCtx *c
             e.old = old;
             a.ulog[base + __popc(mask & below)] = e;
         }
-        if (fresh) {
+        if (early) {
+            a.list[fbase + __popc(fmask & below)] = j;
+            bucket_store<8>(a, j, rid, a.d, slot);
+        } else if (fresh) {
             a.list[fbase + __popc(fmask & below)] = j;
             // into the rebuild's fresh buckets, up to 8 rows at a time
             for (int s0 = 0; s0 < a.d; s0 += 8) {
