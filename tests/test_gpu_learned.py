@@ -53,6 +53,34 @@ def test_mlp_gradient_matches_oracle(rl0):
     assert np.array_equal(g, g2.cpu().numpy().astype(np.float64))
 
 
+@pytest.mark.parametrize("N", [1, 15, 37, 128, 129, 1000])
+def test_mlp_gradient_at_block_edges_matches_oracle(rl0, N):
+    """The tensor-core gradient with a ragged last 16-row tile and 128-sample block
+    (rows past N contribute nothing)."""
+    rng = np.random.default_rng(100 + N)
+    F = (2.0 * rng.standard_normal((N, 16))).astype(np.float32)
+    y = (rng.random(N) < 0.5).astype(np.float32)
+    w = rl0.mlp_init(seed=N)
+    loss, g = rl0.mlp_grad(w, torch.from_numpy(F).cuda(), torch.from_numpy(y).cuda())
+    Lo, go = omlp.loss_and_grad(w.cpu().numpy().astype(np.float64), F.astype(np.float64), y.astype(np.float64))
+    assert loss == pytest.approx(Lo, rel=1e-6)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go)
+
+
+def test_mlp_forward_at_tile_edges_matches_oracle(rl0):
+    rng = np.random.default_rng(7)
+    w = rl0.mlp_init(seed=11)
+    wb = rl0.mlp_export(w)
+    Wf = oracle.bf16_to_f64(wb.cpu().numpy().view(np.uint16))
+    for N in (1, 15, 16, 17, 127, 129):
+        F = rng.standard_normal((N, 16)).astype(np.float32)
+        lg = rl0.mlp_forward(wb, torch.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
+        ref = oracle.mlp_logits(Wf, F.astype(np.float64))
+        assert lg.shape == (N,)
+        assert np.max(np.abs(lg - ref)) <= 1e-5 * (1 + np.max(np.abs(ref)))
+
+
 def test_mlp_forward_matches_oracle_with_bf16_weights(rl0):
     rng = np.random.default_rng(1)
     F = rng.standard_normal((3000, 16)).astype(np.float32)
