@@ -68,6 +68,23 @@ def test_mlp_gradient_at_block_edges_matches_oracle(rl0, N):
     assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go)
 
 
+def test_mlp_training_is_deterministic(rl0):
+    """Two training runs from the same start give bitwise the same parameters and loss:
+    every gradient reduction runs in a fixed order."""
+    rng = np.random.default_rng(5)
+    F = torch.from_numpy(rng.standard_normal((3001, 16)).astype(np.float32)).cuda()
+    Y = torch.from_numpy((rng.random(3001) < 0.4).astype(np.float32)).cuda()
+    out = []
+    for _ in range(2):
+        w = rl0.mlp_init(seed=9)
+        wb, loss = rl0.mlp_train(w, F, Y, epochs=3, batch=500, lr=3e-3)
+        out.append((w.cpu().numpy(), wb.cpu().numpy(), loss))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    w0 = rl0.mlp_init(seed=9)
+    assert not np.array_equal(out[0][0], w0.cpu().numpy())          # it did train
+
+
 def test_mlp_forward_at_tile_edges_matches_oracle(rl0):
     rng = np.random.default_rng(7)
     w = rl0.mlp_init(seed=11)
