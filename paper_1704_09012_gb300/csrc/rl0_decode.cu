@@ -1177,8 +1177,12 @@ static int decode_adaptive(rl0_expander *A, const float *y_dev, int64_t k, const
     return RL0_OK;
 }
 
+// xhat_host (may be NULL): for the plain decode, x_hat is copied there right
+// after the round graph, before the one synchronisation; *copied says whether
+// that happened (the learned and adaptive decodes leave the copy to the caller).
 static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, const rl0_params *params,
-                         float *xhat_dev, rl0_stats *stats, cudaStream_t s)
+                         float *xhat_dev, rl0_stats *stats, cudaStream_t s, float *xhat_host = nullptr,
+                         bool *copied = nullptr)
 {
     rl0_expander *A = const_cast<rl0_expander *>(Ac);
     Resolved R;
@@ -1212,6 +1216,10 @@ static int decode_common(const rl0_expander *Ac, const float *y_dev, int64_t k, 
     if (stats) CK(cudaEventRecord(ev[0], s));
     CK(cudaGraphLaunch(E->exec, s));
     if (stats) CK(cudaEventRecord(ev[1], s));
+    if (xhat_host && !learned) {
+        CK(cudaMemcpyAsync(xhat_host, xhat_dev, (size_t)A->n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (copied) *copied = true;
+    }
     CK(cudaMemcpyAsync(&H->st, w.st, sizeof(DecodeState), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(H->log, w.rlog, R.nrounds * sizeof(RoundLog), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1330,9 +1338,10 @@ extern "C" int rl0_decode_host(const rl0_expander *A, const float *y_host, int64
     cudaError_t e = cudaMallocAsync(&xd, (size_t)A->n * 4, s);
     if (e != cudaSuccess) { cudaFreeAsync(yd, s); return rl0_cuda_err(e); }
     e = cudaMemcpyAsync(yd, y_host, (size_t)A->m * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) rc = decode_common(A, yd, k, params, xd, stats, s);
+    bool copied = false;
+    if (e == cudaSuccess) rc = decode_common(A, yd, k, params, xd, stats, s, xhat_host, &copied);
     else rc = rl0_cuda_err(e);
-    if (rc == RL0_OK) {
+    if (rc == RL0_OK && !copied) {
         e = cudaMemcpyAsync(xhat_host, xd, (size_t)A->n * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         rc = rl0_cuda_err(e);
