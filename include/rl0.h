@@ -178,8 +178,10 @@ int rl0_posterior_mc(const rl0_expander *A, const float *y0_dev, const float *yh
                      uint64_t *hz_dev, uint64_t *he_dev, void *cuda_stream);
 
 /* rl0_decode with host buffers: copies y_host (float[m]) to the device and
- * x_hat back to xhat_host (float[n]) on the stream.  Pinned host memory gives
- * asynchronous copies; pageable memory works too. */
+ * x_hat back to xhat_host (float[n]) on the stream, through device buffers the
+ * expander holds (so calls on one expander must not overlap, as for every
+ * entry point).  Pinned host memory gives asynchronous copies; pageable memory
+ * works too. */
 int rl0_decode_host(const rl0_expander *A, const float *y_host, int64_t k,
                     const rl0_params *params, float *xhat_host, rl0_stats *stats,
                     void *cuda_stream);

@@ -154,6 +154,7 @@ struct Workspace {
     RoundThr *thr;            // per-round thresholds, capacity RL0_MAX_ROUNDS
     RoundLog *rlog;           // per-round log, capacity RL0_MAX_ROUNDS
     double *final_part;       // FP64 residual-norm partials, one set per rz buffer (2 x chunks)
+    float *host_y, *host_x;   // rl0_decode_host's device copies of y_hat (m) and x_hat (n)
     int max_rounds;
 };
 

@@ -889,6 +889,8 @@ int rl0_workspace_alloc(rl0_expander *A)
     al((void **)&w.thr, RL0_MAX_ROUNDS * sizeof(RoundThr));
     al((void **)&w.rlog, RL0_MAX_ROUNDS * sizeof(RoundLog));
     al((void **)&w.final_part, 2 * nchunks * sizeof(double));   // one set per rz buffer
+    al((void **)&w.host_y, m * sizeof(float));
+    al((void **)&w.host_x, n * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(w.bcnt, 0, m * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(w.sbcnt[0], 0, m * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(w.sbcnt[1], 0, m * sizeof(int));
@@ -939,7 +941,7 @@ void rl0_workspace_free(rl0_expander *A)
     }
     void *ptrs[] = {w.rz[0], w.rz[1], w.code[0], w.code[1], w.pzlb, w.res_list, w.list, w.list_tmp, w.ulog, w.dlog, w.bcnt, w.bkt,
                     w.sbcnt[0], w.sbcnt[1], w.sbkt[0], w.sbkt[1], w.l1part, w.hk_scratch, w.st, w.ctx, w.thr, w.rlog,
-                    w.final_part};
+                    w.final_part, w.host_y, w.host_x};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&w, 0, sizeof(w));
 }
@@ -1333,11 +1335,9 @@ extern "C" int rl0_decode_host(const rl0_expander *A, const float *y_host, int64
     int rc = rl0_set_device_of(A);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    float *yd = nullptr, *xd = nullptr;
-    CK(cudaMallocAsync(&yd, (size_t)A->m * 4, s));
-    cudaError_t e = cudaMallocAsync(&xd, (size_t)A->n * 4, s);
-    if (e != cudaSuccess) { cudaFreeAsync(yd, s); return rl0_cuda_err(e); }
-    e = cudaMemcpyAsync(yd, y_host, (size_t)A->m * 4, cudaMemcpyHostToDevice, s);
+    // the expander's own device buffers (calls on one expander are serialised)
+    float *yd = A->ws.host_y, *xd = A->ws.host_x;
+    cudaError_t e = cudaMemcpyAsync(yd, y_host, (size_t)A->m * 4, cudaMemcpyHostToDevice, s);
     bool copied = false;
     if (e == cudaSuccess) rc = decode_common(A, yd, k, params, xd, stats, s, xhat_host, &copied);
     else rc = rl0_cuda_err(e);
@@ -1346,8 +1346,6 @@ extern "C" int rl0_decode_host(const rl0_expander *A, const float *y_host, int64
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         rc = rl0_cuda_err(e);
     }
-    cudaFreeAsync(yd, s);
-    cudaFreeAsync(xd, s);
     return rc;
 }
 
